@@ -1,0 +1,145 @@
+/*
+ * C-ABI of the GB300 Moment Tensor Potential library (libmtp_gb300.so).
+ *
+ * The library evaluates the Moment Tensor Potential (MTP) that the paper
+ * accelerates inside LAMMPS: site energies, forces, the virial (stress), the
+ * parameter gradient and the active-learning extrapolation grade (paper
+ * Sec. 2.1, "Inference computes energies, forces, and stresses"; Sec. 2.1 and
+ * Sec. 2.3 on configuration and neighbourhood mode grades with selection and
+ * break thresholds).  The model itself is the published MTP the paper cites
+ * (Shapeev 2016; MLIP-2/MLIP-3):
+ *
+ *   E_i = s[z_i] + sum_alpha xi_alpha B_alpha(i),  E = sum_i E_i,
+ *   B_alpha: products of full contractions of the moment tensors
+ *   M_{mu,nu}(i) = sum_j f_mu(|r_ij|) rhat_ij^{(x) nu},
+ *   f_mu(r) = sum_k c[mu][k][z_i][z_j] T_k(xi(r)) (R_cut - r)^2.
+ *
+ * Conventions shared by every entry point
+ *   - Units: Angstrom, eV, eV/Angstrom (LAMMPS "metal"); species are 0-based.
+ *   - A cell is 9 doubles on the HOST, row-major, rows are the lattice vectors
+ *     a, b, c; pbc[3] on the HOST, nonzero = periodic along that vector.
+ *   - Positions x are [N][3] doubles in DEVICE memory, Cartesian, anywhere in
+ *     space (they need not be wrapped into the cell).
+ *   - Every array argument is owned by the caller and must stay valid until
+ *     the work queued on `stream` has finished.  `stream` is a cudaStream_t
+ *     passed as void* (NULL = legacy default stream).  Calls are asynchronous
+ *     unless stated otherwise.
+ *   - The library owns handles, neighbour lists and its internal scratch.
+ *     A handle must not be used by two host threads or two streams at once.
+ *   - Every function returns an mtp_status and never aborts; on failure
+ *     mtp_last_error() gives a message (thread-local).
+ *   - Virial order: xx, yy, zz, xy, xz, yz; W = -dE/d(strain), the LAMMPS
+ *     pressure-virial convention.
+ *   - Parameter vector theta (for gradients): [ s (S) | c (n_mu*n_q*S*S, in
+ *     [mu][k][z_i][z_j] order) | xi (m) ].
+ */
+#ifndef MTP_GB300_H
+#define MTP_GB300_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct mtp_handle mtp_handle;
+typedef struct mtp_nlist mtp_nlist;
+
+typedef enum {
+  MTP_OK = 0,
+  MTP_STATUS_BREAK = 1,            /* grade above the break threshold (paper Sec. 2.3) */
+  MTP_ERR_ARG = -1,                /* invalid argument (message says which) */
+  MTP_ERR_CUDA = -2,               /* a CUDA call failed */
+  MTP_ERR_OOM = -3,                /* device allocation failed */
+  MTP_ERR_NEIGHBOR_OVERFLOW = -4,  /* a neighbour image lies beyond +-511 cells */
+  MTP_ERR_NONFINITE = -5,          /* NaN/Inf in inputs or results */
+  MTP_ERR_TIMEOUT = -6,            /* a device-side wait gave up */
+  MTP_ERR_UNSUPPORTED = -7         /* level not compiled into this library */
+} mtp_status;
+
+typedef enum { MTP_FP64 = 0, MTP_MIXED = 1 } mtp_precision;
+
+/* Potential parameters, all HOST pointers, copied by mtp_load_params. */
+typedef struct {
+  int32_t level;                 /* MTP level L (even, 2..20 in this build) */
+  int32_t n_species;             /* S >= 1 */
+  int32_t n_q;                   /* radial basis size, 1..16 */
+  double r_min, r_cut;           /* radial basis interval, 0 <= r_min < r_cut */
+  const double* species_energy;  /* [S] */
+  const double* radial;          /* [n_mu][n_q][S][S]; n_mu = (L - 2) / 4 + 1 */
+  const double* xi;              /* [m] in the library's basis order (mtp_basis_table) */
+  int64_t m;                     /* must equal the basis size of the level */
+} mtp_params_desc;
+
+/* Basis of a level, host only (no GPU needed).
+ * Enumeration: all products of connected contraction graphs of moment tensors
+ * with total level <= L, level(M_{mu,nu}) = 2 + 4 mu + nu, minus functions
+ * linearly dependent on earlier ones.  m: basis size; n_mu: radial functions;
+ * n_comp: symmetric moment components per atom; n_graph: connected graphs. */
+int mtp_basis_info(int32_t level, int32_t* m, int32_t* n_mu, int32_t* n_comp, int32_t* n_graph);
+
+/* Host-only export of the basis tables for bit-exact comparison.
+ * which = 0: graphs, per graph: nv, mu[nv], e[nv(nv-1)/2] (upper triangle, row-major);
+ * which = 1: basis functions, per function: n_factors, graph indices;
+ * which = 2: per graph: n_terms, then per term: integer coefficient and per
+ *            vertex (mu, a, b, c): the graph as a polynomial of the symmetric
+ *            components M_mu[a,b,c] = sum_j f_mu rhat_x^a rhat_y^b rhat_z^c;
+ * which = 3: moment components in kernel order, (mu, a, b, c) each.
+ * Call with buf = NULL to get the length in *len; otherwise *len is the
+ * capacity of buf on input and the number written on output. */
+int mtp_basis_table(int32_t level, int32_t which, int64_t* buf, int64_t* len);
+
+/* Copies the parameters to the current CUDA device.  *out receives a new
+ * handle (free with mtp_free).  Fails with MTP_ERR_UNSUPPORTED for a level
+ * this library was not built for, MTP_ERR_ARG if desc->m differs from the
+ * basis size or a value is out of range. */
+int mtp_load_params(const mtp_params_desc* desc, mtp_handle** out);
+void mtp_free(mtp_handle* h);
+/* Number of entries of theta (see the header comment). */
+int mtp_param_count(const mtp_handle* h, int64_t* n_params);
+
+/* Full neighbour list (paper Sec. 2.3 needs a neighbour list; this one is
+ * full, not half): every (j, n) with r_ij = x_j + n.H - x_i and
+ * 0 < |r_ij|^2 < R_cut^2, n an image vector (zero on open axes), self images
+ * included.  The squared distance is decided in FP64 as (dx*dx + dy*dy) +
+ * dz*dz with d = (x_j + s) - x_i and s = (n1 a + n2 b) + n3 c, every
+ * operation rounded separately.  Per atom the entries are sorted by
+ * (j, n1, n2, n3).  R_cut comes from the handle.
+ * *inout: NULL to create a list, or an existing list to rebuild in place
+ * (its storage grows when needed).  Synchronises `stream` (the pair count
+ * sizes the list).  MTP_ERR_NEIGHBOR_OVERFLOW if an image exceeds +-511. */
+int mtp_build_neighbors(mtp_handle* h, const double* x_dev, int64_t n_atoms, const double* cell,
+                        const int32_t* pbc, mtp_nlist** inout, void* stream);
+int mtp_nlist_info(const mtp_nlist* nl, int64_t* n_atoms, int64_t* n_pairs);
+/* Copies the list to caller DEVICE arrays: offsets [N+1] (int64), j [P]
+ * (int32), images [P][3] (int32). */
+int mtp_nlist_copy(const mtp_nlist* nl, int64_t* offsets_dev, int32_t* j_dev, int32_t* img_dev, void* stream);
+void mtp_free_nlist(mtp_nlist* nl);
+
+/* Energies, forces, virial and (optionally) dE/dtheta for one configuration.
+ * x_dev [N][3], z_dev [N] (int32 species); nl built for these atoms (positions
+ * may have moved since, the list is used as is).  cell: host [9], the current
+ * cell (image shifts are n.H with this H).
+ * precision: MTP_FP64, or MTP_MIXED (radial basis, moments, contractions and
+ * the adjoint in FP32; pair vectors from 32.32 fixed-point fractional
+ * coordinates; energies, forces, virial and gradients accumulated in FP64).
+ * chunk_atoms: centre atoms per launch (paper Sec. 2.3 "chunksize"); 0 = all.
+ * Outputs (DEVICE, overwritten): e_atom [N], forces [N][3], virial [6],
+ * e_total [1]; dEdtheta [n_params] or NULL to skip the parameter gradient. */
+int mtp_compute_efv(mtp_handle* h, const mtp_nlist* nl, const double* x_dev, const int32_t* z_dev,
+                    int64_t n_atoms, const double* cell, int32_t precision, int64_t chunk_atoms,
+                    double* e_atom_dev, double* forces_dev, double* virial_dev, double* e_total_dev,
+                    double* dEdtheta_dev, void* stream);
+
+/* Device status word of the handle: the first device-side error recorded
+ * since the last call (non-finite site energy or force, ...), then cleared.
+ * Synchronises `stream`. */
+int mtp_device_status(mtp_handle* h, void* stream);
+
+/* Human-readable message for the last failure on this thread. */
+const char* mtp_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MTP_GB300_H */

@@ -1,0 +1,235 @@
+"""GB300-native Moment Tensor Potential evaluation.
+
+A thin binding over the C-ABI of libmtp_gb300.so (include/mtp.h): every
+function here only marshals arguments; neighbour lists, energies, forces,
+virials, parameter gradients and grades are computed by the library's CUDA
+kernels.  Device arrays are torch tensors on the current CUDA device (torch is
+used for device memory and streams only).
+"""
+from __future__ import annotations
+
+import ctypes
+import json
+
+import numpy as np
+
+from . import _lib
+from ._lib import MTP_FP64, MTP_MIXED, MtpError, check
+
+__all__ = [
+    "MTP_FP64", "MTP_MIXED", "MtpError", "Potential", "NeighborList", "mtp_basis_info", "mtp_basis_table",
+    "mtp_load_params", "mtp_build_neighbors", "mtp_compute_efv", "mtp_device_status", "library_path",
+]
+
+
+def library_path() -> str:
+    return _lib.LIB_PATH
+
+
+def _stream_ptr(stream):
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _dptr(t, dtype=None, n=None, name="array"):
+    import torch
+    if t is None:
+        return None
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError("%s must be a CUDA tensor" % name)
+    if dtype is not None and t.dtype != dtype:
+        raise TypeError("%s must have dtype %s (got %s)" % (name, dtype, t.dtype))
+    if not t.is_contiguous():
+        raise ValueError("%s must be contiguous" % name)
+    if n is not None and t.numel() != n:
+        raise ValueError("%s must have %d elements (got %d)" % (name, n, t.numel()))
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _host_d(a, n):
+    a = np.ascontiguousarray(np.asarray(a, dtype=np.float64).reshape(-1))
+    if a.size != n:
+        raise ValueError("expected %d values, got %d" % (n, a.size))
+    return a
+
+
+def mtp_basis_info(level: int) -> dict:
+    """Basis size m, radial functions n_mu, moment components, graphs (host only)."""
+    lib = _lib.load()
+    m, nmu, nc, ng = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
+    check(lib.mtp_basis_info(level, ctypes.byref(m), ctypes.byref(nmu), ctypes.byref(nc), ctypes.byref(ng)))
+    return {"m": m.value, "n_mu": nmu.value, "n_comp": nc.value, "n_graph": ng.value}
+
+
+def mtp_basis_table(level: int, which: int) -> np.ndarray:
+    """Raw int64 table (0 graphs, 1 basis functions, 2 polynomials, 3 components)."""
+    lib = _lib.load()
+    n = ctypes.c_int64()
+    check(lib.mtp_basis_table(level, which, None, ctypes.byref(n)))
+    buf = np.zeros(max(1, n.value), dtype=np.int64)
+    check(lib.mtp_basis_table(level, which, buf.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)), ctypes.byref(n)))
+    return buf[:n.value]
+
+
+def decode_basis(level: int):
+    """(graphs, bases): graphs as (mu tuple, e tuple), bases as tuples of graph indices."""
+    g = mtp_basis_table(level, 0).tolist()
+    graphs = []
+    k = 0
+    while k < len(g):
+        nv = g[k]
+        mu = tuple(g[k + 1:k + 1 + nv])
+        ne = nv * (nv - 1) // 2
+        e = tuple(g[k + 1 + nv:k + 1 + nv + ne])
+        graphs.append((mu, e))
+        k += 1 + nv + ne
+    b = mtp_basis_table(level, 1).tolist()
+    bases = []
+    k = 0
+    while k < len(b):
+        nf = b[k]
+        bases.append(tuple(b[k + 1:k + 1 + nf]))
+        k += 1 + nf
+    return graphs, bases
+
+
+class Potential:
+    """Owns an mtp_handle (parameters resident on the current device)."""
+
+    def __init__(self, level, n_species, n_q, r_min, r_cut, species_energy, radial, xi):
+        lib = _lib.load()
+        info = mtp_basis_info(level)
+        self.level, self.n_species, self.n_q = int(level), int(n_species), int(n_q)
+        self.r_min, self.r_cut = float(r_min), float(r_cut)
+        self.n_mu = info["n_mu"]
+        self.m = info["m"]
+        s = _host_d(species_energy, n_species)
+        c = _host_d(radial, self.n_mu * n_q * n_species * n_species)
+        x = _host_d(xi, len(np.asarray(xi).reshape(-1)))
+        dp = lambda a: a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))  # noqa: E731
+        desc = _lib.ParamsDesc(self.level, self.n_species, self.n_q, self.r_min, self.r_cut, dp(s), dp(c), dp(x),
+                               x.size)
+        h = ctypes.c_void_p()
+        check(lib.mtp_load_params(ctypes.byref(desc), ctypes.byref(h)))
+        self._h = h
+        n = ctypes.c_int64()
+        check(lib.mtp_param_count(h, ctypes.byref(n)))
+        self.n_params = n.value
+
+    @classmethod
+    def from_dict(cls, pot: dict, check_basis: bool = True):
+        """From a potential dictionary (potentials/*.json).  With check_basis the
+        file's basis encoding must equal the library's own basis."""
+        if check_basis and "basis" in pot:
+            graphs, bases = decode_basis(pot["level"])
+            mine = [[[list(graphs[k][0]), list(graphs[k][1])] for k in b] for b in bases]
+            if mine != pot["basis"]:
+                raise ValueError("potential basis differs from the library basis for level %d" % pot["level"])
+        return cls(pot["level"], pot["n_species"], pot["n_q"], pot["r_min"], pot["r_cut"], pot["species_energy"],
+                   pot["radial"], pot["xi"])
+
+    @classmethod
+    def from_file(cls, path: str, check_basis: bool = True):
+        with open(path) as fh:
+            return cls.from_dict(json.load(fh), check_basis)
+
+    @property
+    def handle(self):
+        return self._h
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h is not None and h.value:
+            try:
+                _lib.load().mtp_free(h)
+            except Exception:
+                pass
+            self._h = None
+
+
+class NeighborList:
+    """Owns an mtp_nlist."""
+
+    def __init__(self):
+        self._nl = ctypes.c_void_p()
+
+    @property
+    def handle(self):
+        return self._nl
+
+    def info(self):
+        a, p = ctypes.c_int64(), ctypes.c_int64()
+        check(_lib.load().mtp_nlist_info(self._nl, ctypes.byref(a), ctypes.byref(p)))
+        return a.value, p.value
+
+    def to_tensors(self, stream=None):
+        """(offsets [N+1] int64, j [P] int32, images [P, 3] int32) on the device."""
+        import torch
+        n, p = self.info()
+        dev = torch.device("cuda", torch.cuda.current_device())
+        off = torch.empty(n + 1, dtype=torch.int64, device=dev)
+        j = torch.empty(max(p, 1), dtype=torch.int32, device=dev)
+        img = torch.empty((max(p, 1), 3), dtype=torch.int32, device=dev)
+        check(_lib.load().mtp_nlist_copy(self._nl, _dptr(off), _dptr(j), _dptr(img), _stream_ptr(stream)))
+        return off, j[:p], img[:p]
+
+    def __del__(self):
+        nl = getattr(self, "_nl", None)
+        if nl is not None and nl.value:
+            try:
+                _lib.load().mtp_free_nlist(nl)
+            except Exception:
+                pass
+            self._nl = None
+
+
+def mtp_load_params(pot: dict) -> Potential:
+    return Potential.from_dict(pot)
+
+
+def mtp_build_neighbors(potential: Potential, x, cell, pbc=(1, 1, 1), nlist: NeighborList | None = None,
+                        stream=None) -> NeighborList:
+    """Full neighbour list of x ([N, 3] float64 CUDA tensor) in the given cell."""
+    import torch
+    n = x.shape[0] if x.dim() == 2 else 0
+    nl = nlist if nlist is not None else NeighborList()
+    c = _host_d(cell, 9)
+    p = np.ascontiguousarray(np.asarray(pbc, dtype=np.int32).reshape(3))
+    check(_lib.load().mtp_build_neighbors(
+        potential.handle, _dptr(x, torch.float64, 3 * n, "x"), n, c.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+        p.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), ctypes.byref(nl.handle), _stream_ptr(stream)))
+    return nl
+
+
+def mtp_compute_efv(potential: Potential, nlist: NeighborList, x, z, cell, precision=MTP_MIXED, chunk_atoms=0,
+                    dtheta=False, out=None, stream=None) -> dict:
+    """Site energies, forces, virial, total energy and optionally dE/dtheta.
+
+    x: [N, 3] float64, z: [N] int32 (CUDA tensors).  Returns a dict of CUDA
+    tensors (e_atom [N], forces [N, 3], virial [6], e_total [1], dtheta or None);
+    pass ``out`` (a dict from an earlier call) to reuse its storage."""
+    import torch
+    n = x.shape[0]
+    dev = x.device
+    if out is None:
+        out = {
+            "e_atom": torch.empty(n, dtype=torch.float64, device=dev),
+            "forces": torch.empty((n, 3), dtype=torch.float64, device=dev),
+            "virial": torch.empty(6, dtype=torch.float64, device=dev),
+            "e_total": torch.empty(1, dtype=torch.float64, device=dev),
+            "dtheta": torch.empty(potential.n_params, dtype=torch.float64, device=dev) if dtheta else None,
+        }
+    c = _host_d(cell, 9)
+    check(_lib.load().mtp_compute_efv(
+        potential.handle, nlist.handle, _dptr(x, torch.float64, 3 * n, "x"), _dptr(z, torch.int32, n, "z"), n,
+        c.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), int(precision), int(chunk_atoms),
+        _dptr(out["e_atom"], torch.float64, n, "e_atom"), _dptr(out["forces"], torch.float64, 3 * n, "forces"),
+        _dptr(out["virial"], torch.float64, 6, "virial"), _dptr(out["e_total"], torch.float64, 1, "e_total"),
+        _dptr(out["dtheta"], torch.float64, potential.n_params, "dtheta") if dtheta else None, _stream_ptr(stream)))
+    return out
+
+
+def mtp_device_status(potential: Potential, stream=None) -> int:
+    """Device-side status since the last check (0 = fine); raises on error."""
+    return check(_lib.load().mtp_device_status(potential.handle, _stream_ptr(stream)))

@@ -1,0 +1,751 @@
+"""Build-time generator of the MTP basis and its straight-line CUDA code.
+
+For a level L this module
+  1. enumerates the connected contraction graphs of moment tensors with total
+     level <= L and all their products (the basis functions B_alpha of the
+     Moment Tensor Potential, Shapeev 2016, the model the paper accelerates;
+     paper Sec. 2.2 on the level),
+  2. removes basis functions that are linear combinations of earlier ones, by
+     exact rank computations over the prime field GF(2^31 - 1) at random points
+     of the unit sphere (a rational parametrisation, so |u| = 1 holds exactly),
+  3. expands each graph into an integer polynomial of symmetric moment
+     components with the multinomial theorem (exported for table checks),
+  4. factors every graph into a DAG of symmetric contractions with shared
+     subexpressions, and
+  5. writes a C++/CUDA header with the moment layout, straight-line device
+     code for the per-pair moment update, the per-atom contraction with its
+     reverse pass, the per-pair adjoint, and host tables of the basis.
+
+Canonical forms and the order of basis functions (shared by every consumer of
+the table):
+  * a graph is the lexicographically smallest (mu tuple, upper-triangle edge
+    multiplicity tuple) over vertex orderings; its sort key is
+    (level, mu tuple, edge tuple);
+  * a basis function is a multiset of graphs sorted by that key; basis
+    functions are ordered by (level, number of factors, factor keys);
+  * moment components are ordered by (mu, nu) and, within a tensor, by
+    (a, b, c) with a descending, then b descending (powers of x, y, z).
+"""
+from __future__ import annotations
+
+import itertools
+import math
+import os
+import sys
+from collections import defaultdict
+
+import numpy as np
+
+# ---------------------------------------------------------------------------
+# graphs and basis functions
+# ---------------------------------------------------------------------------
+
+
+def level_of_moment(mu, nu):
+    return 2 + 4 * mu + nu
+
+
+def radial_count(level):
+    return (level - 2) // 4 + 1
+
+
+def multi_indices(n):
+    """(a, b, c) with a + b + c = n, a descending, then b descending."""
+    return [(a, b, n - a - b) for a in range(n, -1, -1) for b in range(n - a, -1, -1)]
+
+
+def n_sym(n):
+    return (n + 1) * (n + 2) // 2
+
+
+class G:
+    """A canonical connected graph."""
+    __slots__ = ("mu", "e", "nv", "nu", "level", "edges")
+
+    def __init__(self, mu, e):
+        self.mu = tuple(mu)
+        self.e = tuple(e)
+        self.nv = len(mu)
+        pairs = [(v, w) for v in range(self.nv) for w in range(v + 1, self.nv)]
+        self.edges = {p: k for p, k in zip(pairs, e) if k}
+        nu = [0] * self.nv
+        for (v, w), k in self.edges.items():
+            nu[v] += k
+            nu[w] += k
+        self.nu = tuple(nu)
+        self.level = sum(level_of_moment(m, n) for m, n in zip(self.mu, self.nu))
+
+    @property
+    def key(self):
+        return (self.level, self.mu, self.e)
+
+
+def _block_perms(mu_sorted):
+    """Permutations of vertex positions that keep the sorted labels sorted."""
+    blocks = []
+    start = 0
+    for k in range(1, len(mu_sorted) + 1):
+        if k == len(mu_sorted) or mu_sorted[k] != mu_sorted[start]:
+            blocks.append(list(range(start, k)))
+            start = k
+    for parts in itertools.product(*[itertools.permutations(b) for b in blocks]):
+        yield [v for part in parts for v in part]
+
+
+def _canonical(mu_sorted, mat):
+    n = len(mu_sorted)
+    best = None
+    for p in _block_perms(mu_sorted):
+        e = tuple(mat[p[a]][p[b]] for a in range(n) for b in range(a + 1, n))
+        if best is None or e < best:
+            best = e
+    return tuple(mu_sorted), best
+
+
+def _connected(n, mat):
+    reach = {0}
+    frontier = [0]
+    while frontier:
+        nxt = []
+        for v in frontier:
+            for w in range(n):
+                if mat[v][w] and w not in reach:
+                    reach.add(w)
+                    nxt.append(w)
+        frontier = nxt
+    return len(reach) == n
+
+
+def graphs_for_level(level):
+    """Canonical connected graphs, sorted by key.  Labels are generated as
+    non-decreasing tuples, so only permutations inside blocks of equal labels
+    are needed to canonicalise."""
+    nmu = radial_count(level)
+    seen = set()
+    nv = 1
+    while 2 * nv + 2 * (nv - 1) <= level:
+        pairs = [(v, w) for v in range(nv) for w in range(v + 1, nv)]
+        budget = (level - 2 * nv) // 2          # edges allowed
+        for labels in itertools.combinations_with_replacement(range(nmu), nv):
+            spare = (level - 2 * nv - 4 * sum(labels)) // 2
+            if spare < (nv - 1):
+                continue
+            cap = min(budget, spare)
+
+            def fill(k, left, mult):
+                if k == len(pairs):
+                    yield list(mult)
+                    return
+                for x in range(left + 1):
+                    mult.append(x)
+                    yield from fill(k + 1, left - x, mult)
+                    mult.pop()
+
+            for mult in fill(0, cap, []):
+                mat = [[0] * nv for _ in range(nv)]
+                for (v, w), x in zip(pairs, mult):
+                    mat[v][w] = mat[w][v] = x
+                if nv > 1 and not _connected(nv, mat):
+                    continue
+                seen.add(_canonical(labels, mat))
+        nv += 1
+    out = [G(mu, e) for mu, e in seen]
+    out.sort(key=lambda g: g.key)
+    return out
+
+
+def products_for_level(level, graphs):
+    """All multisets of graphs with total level <= L, in canonical order."""
+    res = []
+    levels = [g.level for g in graphs]
+
+    def walk(first, acc, lev):
+        for k in range(first, len(graphs)):
+            if lev + levels[k] > level:
+                continue
+            acc.append(k)
+            res.append(tuple(acc))
+            walk(k, acc, lev + levels[k])
+            acc.pop()
+
+    walk(0, [], 0)
+    res.sort(key=lambda b: (sum(levels[k] for k in b), len(b), tuple(graphs[k].key for k in b)))
+    return res
+
+
+# ---------------------------------------------------------------------------
+# multinomial expansion into symmetric components
+# ---------------------------------------------------------------------------
+
+
+def multinomial_weight(k):
+    n = sum(k)
+    return math.factorial(n) // (math.factorial(k[0]) * math.factorial(k[1]) * math.factorial(k[2]))
+
+
+def expand_graph(g: G):
+    """{monomial: integer coefficient}; a monomial is a sorted tuple of
+    (mu, (a, b, c)) per vertex.  Each edge of multiplicity e expands
+    (u_v . u_w)^e = sum_{|k|=e} e!/k! u_v^k u_w^k."""
+    edges = sorted(g.edges.items())
+    poly = defaultdict(int)
+    for choice in itertools.product(*[multi_indices(e) for _, e in edges]):
+        weight = 1
+        acc = [[0, 0, 0] for _ in range(g.nv)]
+        for ((v, w), _), k in zip(edges, choice):
+            weight *= multinomial_weight(k)
+            for d in range(3):
+                acc[v][d] += k[d]
+                acc[w][d] += k[d]
+        mono = tuple(sorted((g.mu[v], tuple(acc[v])) for v in range(g.nv)))
+        poly[mono] += weight
+    return dict(poly)
+
+
+# ---------------------------------------------------------------------------
+# exact pruning over GF(p)
+# ---------------------------------------------------------------------------
+
+PRIME = 2147483647  # 2^31 - 1
+
+
+def _inv(a):
+    return pow(int(a), PRIME - 2, PRIME)
+
+
+def _sphere_points(rng, count):
+    """Points (x, y, z) of GF(p)^3 with x^2 + y^2 + z^2 = 1 (inverse
+    stereographic projection of random (s, t))."""
+    pts = []
+    while len(pts) < count:
+        s, t = (int(v) for v in rng.integers(0, PRIME, size=2))
+        q = (s * s + t * t + 1) % PRIME
+        if q == 0:
+            continue
+        qi = _inv(q)
+        pts.append(((2 * s * qi) % PRIME, (2 * t * qi) % PRIME, ((s * s + t * t - 1) * qi) % PRIME))
+    return np.array(pts, dtype=np.int64)
+
+
+def _mod_rank_greedy(cols):
+    """Indices of columns independent of all earlier kept columns (GF(p))."""
+    n_rows = cols.shape[0]
+    piv_rows = []       # pivot row of each kept column's reduced vector
+    reduced = []        # reduced kept vectors
+    kept = []
+    for k in range(cols.shape[1]):
+        v = cols[:, k].copy() % PRIME
+        for pr, rv in zip(piv_rows, reduced):
+            if v[pr]:
+                v = (v - (int(v[pr]) * rv) % PRIME) % PRIME
+        nz = np.nonzero(v)[0]
+        if nz.size:
+            pr = int(nz[0])
+            v = (v * _inv(v[pr])) % PRIME
+            piv_rows.append(pr)
+            reduced.append(v)
+            kept.append(k)
+    del n_rows
+    return kept
+
+
+def prune(level, graphs, products, seed=20251017):
+    """Keep the basis functions that are linearly independent of earlier ones
+    as polynomials in (u_j, f_mu(j)) with |u_j| = 1."""
+    rng = np.random.default_rng(seed)
+    nmu = radial_count(level)
+    n_hood = 2 * len(products) + 8
+    n_nb = 12
+    layout = sorted({(m, n) for g in graphs for m, n in zip(g.mu, g.nu)})
+    maxnu = max(n for _, n in layout)
+    pts = _sphere_points(rng, n_hood * n_nb).reshape(n_hood, n_nb, 3)
+    f = rng.integers(0, PRIME, size=(n_hood, n_nb, nmu), dtype=np.int64)
+    # powers of each coordinate
+    pw = np.ones((maxnu + 1, n_hood, n_nb, 3), dtype=np.int64)
+    for k in range(1, maxnu + 1):
+        pw[k] = (pw[k - 1] * pts) % PRIME
+    comp = {}
+    for mu, nu in layout:
+        for K in multi_indices(nu):
+            mono = (pw[K[0], :, :, 0] * pw[K[1], :, :, 1]) % PRIME
+            mono = (mono * pw[K[2], :, :, 2]) % PRIME
+            comp[(mu, K)] = ((mono * f[:, :, mu]) % PRIME).sum(axis=1) % PRIME
+    gval = []
+    for g in graphs:
+        acc = np.zeros(n_hood, dtype=np.int64)
+        for mono, coef in expand_graph(g).items():
+            t = np.full(n_hood, coef % PRIME, dtype=np.int64)
+            for key in mono:
+                t = (t * comp[key]) % PRIME
+            acc = (acc + t) % PRIME
+        gval.append(acc)
+    cols = np.zeros((n_hood, len(products)), dtype=np.int64)
+    for a, b in enumerate(products):
+        v = np.ones(n_hood, dtype=np.int64)
+        for k in b:
+            v = (v * gval[k]) % PRIME
+        cols[:, a] = v
+    return _mod_rank_greedy(cols)
+
+
+# ---------------------------------------------------------------------------
+# contraction DAG
+# ---------------------------------------------------------------------------
+
+
+class Dag:
+    """Nodes are symmetric tensors stored by multi_indices(rank) components.
+
+    ('M', mu, nu, off): slice of M_{mu,nu}: component K -> M_mu[off + K],
+                        rank nu - |off|.
+    ('C', A, B):        B (rank p) fully contracted into A (rank >= p):
+                        C[K] = sum_{|P| = p} p!/P! A[K + P] B[P].
+    """
+
+    def __init__(self):
+        self.nodes = []      # list of (kind, ...), rank
+        self.index = {}
+
+    def _add(self, key, rank):
+        if key not in self.index:
+            self.index[key] = len(self.nodes)
+            self.nodes.append((key, rank))
+        return self.index[key]
+
+    def rank(self, n):
+        return self.nodes[n][1]
+
+    def leaf(self, mu, nu, off):
+        return self._add(("M", mu, nu, tuple(off)), nu - sum(off))
+
+    def contract(self, a, b):
+        ra, rb = self.rank(a), self.rank(b)
+        if ra < rb:
+            a, b, ra, rb = b, a, rb, ra
+        key = ("C",) + ((min(a, b), max(a, b)) if ra == rb else (a, b))
+        return self._add(key, ra - rb)
+
+    def graph(self, g: G):
+        """[(weight, scalar node)] whose weighted sum is the graph value."""
+        if g.nv == 1:
+            return [(1, self.leaf(g.mu[0], 0, (0, 0, 0)))]
+        # spanning tree by breadth-first search from vertex 0, lowest index first
+        tree = set()
+        seen = {0}
+        queue = [0]
+        while queue:
+            v = queue.pop(0)
+            for (a, b) in sorted(g.edges):
+                if v in (a, b):
+                    w = b if a == v else a
+                    if w not in seen:
+                        seen.add(w)
+                        tree.add((a, b))
+                        queue.append(w)
+        cut = sorted(p for p in g.edges if p not in tree)
+        out = []
+        for choice in itertools.product(*[multi_indices(g.edges[p]) for p in cut]):
+            weight = 1
+            off = [[0, 0, 0] for _ in range(g.nv)]
+            for p, k in zip(cut, choice):
+                weight *= multinomial_weight(k)
+                for v in p:
+                    for d in range(3):
+                        off[v][d] += k[d]
+            cur = {v: self.leaf(g.mu[v], g.nu[v], off[v]) for v in range(g.nv)}
+            nbrs = {v: set() for v in range(g.nv)}
+            for (a, b) in tree:
+                nbrs[a].add(b)
+                nbrs[b].add(a)
+            alive = set(range(g.nv))
+            while len(alive) > 1:
+                leaves = [v for v in alive if len(nbrs[v]) == 1]
+                v = min(leaves, key=lambda t: (self.rank(cur[t]), t))
+                (w,) = nbrs[v]
+                cur[w] = self.contract(cur[w], cur[v])
+                nbrs[w].discard(v)
+                nbrs.pop(v)
+                alive.discard(v)
+            out.append((weight, cur[alive.pop()]))
+        return out
+
+
+# ---------------------------------------------------------------------------
+# the level description
+# ---------------------------------------------------------------------------
+
+
+class Level:
+    def __init__(self, level):
+        self.level = level
+        self.nmu = radial_count(level)
+        all_graphs = graphs_for_level(level)
+        all_products = products_for_level(level, all_graphs)
+        kept = prune(level, all_graphs, all_products)
+        self.n_enumerated = len(all_products)
+        used = sorted({k for a in kept for k in all_products[a]})
+        remap = {k: i for i, k in enumerate(used)}
+        self.graphs = [all_graphs[k] for k in used]
+        self.bases = [tuple(remap[k] for k in all_products[a]) for a in kept]
+        self.layout = sorted({(m, n) for g in self.graphs for m, n in zip(g.mu, g.nu)})
+        self.nu_max = [max([n for m, n in self.layout if m == mu], default=-1) for mu in range(self.nmu)]
+        self.comps = [(mu, K) for mu, nu in self.layout for K in multi_indices(nu)]
+        self.comp_index = {c: i for i, c in enumerate(self.comps)}
+        self.dag = Dag()
+        self.roots = [self.dag.graph(g) for g in self.graphs]
+
+    @property
+    def m(self):
+        return len(self.bases)
+
+
+# ---------------------------------------------------------------------------
+# code emission
+# ---------------------------------------------------------------------------
+
+
+def _mono_name(K):
+    return "u%d%d%d" % K
+
+
+def _emit_monomials(lines, maxnu, ind, need=None):
+    """u^K for all |K| <= maxnu, each from a lower one times one coordinate."""
+    lines.append(ind + "const R u000 = R(1);")
+    for nu in range(1, maxnu + 1):
+        for K in multi_indices(nu):
+            if need is not None and K not in need:
+                continue
+            if K[0] > 0:
+                src, c = (K[0] - 1, K[1], K[2]), "ux"
+            elif K[1] > 0:
+                src, c = (K[0], K[1] - 1, K[2]), "uy"
+            else:
+                src, c = (K[0], K[1], K[2] - 1), "uz"
+            lines.append(ind + "const R %s = %s * %s;" % (_mono_name(K), _mono_name(src), c))
+
+
+def _closure(keys):
+    """All monomials needed to build ``keys`` by the rule in _emit_monomials."""
+    need = set()
+    for K in keys:
+        k = tuple(K)
+        while sum(k) > 0:
+            need.add(k)
+            if k[0] > 0:
+                k = (k[0] - 1, k[1], k[2])
+            elif k[1] > 0:
+                k = (k[0], k[1] - 1, k[2])
+            else:
+                k = (k[0], k[1], k[2] - 1)
+    return need
+
+
+def emit_moments(lv: Level):
+    """M[c] += f[mu] * u^K for every component (mu, K)."""
+    L = []
+    ind = "    "
+    L.append("  template <class R>")
+    L.append("  __device__ __forceinline__ static void moments(R* __restrict__ M, const R* __restrict__ f, R ux, R uy, R uz) {")
+    _emit_monomials(L, max(lv.nu_max), ind)
+    for c, (mu, K) in enumerate(lv.comps):
+        L.append(ind + "M[%d] = fmadd(f[%d], %s, M[%d]);" % (c, mu, _mono_name(K), c))
+    L.append("  }")
+    return L
+
+
+def emit_pair_adjoint(lv: Level):
+    """Gradient of sum_c D[c] M_c(r) with respect to the pair vector r, where
+    M_c(r) = f_mu(|r|) rhat^K:
+
+        S_mu = sum_K D u^K,  T_mu = sum_K |K| D u^K,  G_mu = sum_K D grad_u(u^K)
+        g = u * sum_mu (df_mu S_mu - f_mu T_mu / r) + (1/r) sum_mu f_mu G_mu
+
+    (grad of u^K along the sphere is (grad_u u^K - |K| u^K u) / r).  S_mu is
+    also returned: it is the chain-rule factor of d E / d c[mu, k, zi, zj]."""
+    L = []
+    ind = "    "
+    L.append("  template <class R>")
+    L.append("  __device__ __forceinline__ static void pair_adjoint(const R* __restrict__ D, const R* __restrict__ f, "
+             "const R* __restrict__ df, R ux, R uy, R uz, R rinv, R& gx, R& gy, R& gz, R* __restrict__ S) {")
+    _emit_monomials(L, max(lv.nu_max), ind)
+    L.append(ind + "R ax = R(0), ay = R(0), az = R(0), radial = R(0);")
+    for mu in range(lv.nmu):
+        comps = [(c, K) for c, (m, K) in enumerate(lv.comps) if m == mu]
+        if not comps:
+            L.append(ind + "S[%d] = R(0);" % mu)
+            continue
+        bynu = defaultdict(list)
+        for c, K in comps:
+            bynu[sum(K)].append((c, K))
+        # S_{mu,nu}
+        for nu, lst in sorted(bynu.items()):
+            c0, K0 = lst[0]
+            expr = "D[%d] * %s" % (c0, _mono_name(K0))
+            L.append(ind + "R s%d_%d = %s;" % (mu, nu, expr))
+            for c, K in lst[1:]:
+                L.append(ind + "s%d_%d = fmadd(D[%d], %s, s%d_%d);" % (mu, nu, c, _mono_name(K), mu, nu))
+        nus = sorted(bynu)
+        L.append(ind + "const R S%d = %s;" % (mu, " + ".join("s%d_%d" % (mu, n) for n in nus)))
+        tnus = [n for n in nus if n > 0]
+        if tnus:
+            L.append(ind + "const R T%d = %s;" % (mu, " + ".join(("s%d_%d" % (mu, n)) if n == 1 else
+                                                                ("R(%d) * s%d_%d" % (n, mu, n)) for n in tnus)))
+        else:
+            L.append(ind + "const R T%d = R(0);" % mu)
+        L.append(ind + "S[%d] = S%d;" % (mu, mu))
+        # G_mu grouped by the integer factor K_d
+        for d, dn in enumerate("xyz"):
+            groups = defaultdict(list)
+            for c, K in comps:
+                if K[d] > 0:
+                    low = list(K)
+                    low[d] -= 1
+                    groups[K[d]].append((c, tuple(low)))
+            parts = []
+            for a, lst in sorted(groups.items()):
+                name = "g%d%s%d" % (mu, dn, a)
+                c0, k0 = lst[0]
+                L.append(ind + "R %s = D[%d] * %s;" % (name, c0, _mono_name(k0)))
+                for c, k in lst[1:]:
+                    L.append(ind + "%s = fmadd(D[%d], %s, %s);" % (name, c, _mono_name(k), name))
+                parts.append(name if a == 1 else "R(%d) * %s" % (a, name))
+            if parts:
+                L.append(ind + "a%s = fmadd(f[%d], %s, a%s);" % (dn, mu, " + ".join(parts), dn))
+        L.append(ind + "radial = fmadd(df[%d], S%d, radial);" % (mu, mu))
+        L.append(ind + "radial = fmadd(-f[%d] * rinv, T%d, radial);" % (mu, mu))
+    L.append(ind + "gx = fmadd(ux, radial, ax * rinv);")
+    L.append(ind + "gy = fmadd(uy, radial, ay * rinv);")
+    L.append(ind + "gz = fmadd(uz, radial, az * rinv);")
+    L.append("  }")
+    return L
+
+
+def emit_contract(lv: Level):
+    """Per atom: graph values from the DAG, basis products, E = sum xi B, and the
+    reverse pass D = dE/dM.  ``WANT_B`` stores the basis values."""
+    dag = lv.dag
+    L = []
+    ind = "    "
+    L.append("  template <class R, bool WANT_B>")
+    L.append("  __device__ __forceinline__ static R contract(const R* __restrict__ M, "
+             "const typename ScalarOf<R>::T* __restrict__ xi, R* __restrict__ D, R* __restrict__ B) {")
+    L.append(ind + "(void)B;")
+    # forward
+    def comp_ref(n, K):
+        key, rank = dag.nodes[n]
+        if key[0] == "M":
+            _, mu, nu, off = key
+            full = (off[0] + K[0], off[1] + K[1], off[2] + K[2])
+            return "M[%d]" % lv.comp_index[(mu, full)]
+        return "v%d_%d" % (n, multi_indices(rank).index(K))
+
+    wname = {}
+    for n, (key, rank) in enumerate(dag.nodes):
+        if key[0] != "C":
+            continue
+        _, a, b = key
+        p = dag.rank(b)
+        Ps = multi_indices(p)
+        # weighted copy of B's components (weights p!/P!)
+        wn = []
+        for P in Ps:
+            w = multinomial_weight(P)
+            if w == 1:
+                wn.append(comp_ref(b, P))
+            else:
+                nm = "w%d_%d" % (n, Ps.index(P))
+                L.append(ind + "const R %s = R(%d) * %s;" % (nm, w, comp_ref(b, P)))
+                wn.append(nm)
+        wname[n] = wn
+        for ki, K in enumerate(multi_indices(rank)):
+            terms = [(comp_ref(a, (K[0] + P[0], K[1] + P[1], K[2] + P[2])), wn[j]) for j, P in enumerate(Ps)]
+            expr = "%s * %s" % terms[0]
+            L.append(ind + "R v%d_%d = %s;" % (n, ki, expr))
+            for x, y in terms[1:]:
+                L.append(ind + "v%d_%d = fmadd(%s, %s, v%d_%d);" % (n, ki, x, y, n, ki))
+    # graph values
+    for gi, roots in enumerate(lv.roots):
+        parts = []
+        for w, node in roots:
+            ref = comp_ref(node, (0, 0, 0))
+            parts.append(ref if w == 1 else "R(%d) * %s" % (w, ref))
+        L.append(ind + "const R G%d = %s;" % (gi, " + ".join(parts)))
+    # basis values, energy
+    L.append(ind + "R E = R(0);")
+    for a, b in enumerate(lv.bases):
+        L.append(ind + "const R B%d = %s;" % (a, " * ".join("G%d" % k for k in b)))
+        L.append(ind + "if (WANT_B) B[%d] = B%d;" % (a, a))
+        L.append(ind + "E = fmadd(R(xi[%d]), B%d, E);" % (a, a))
+    # reverse: dE/dG
+    gbar = defaultdict(list)
+    for a, b in enumerate(lv.bases):
+        for j in range(len(b)):
+            others = [b[t] for t in range(len(b)) if t != j]
+            gbar[b[j]].append((a, others))
+    for gi in range(len(lv.graphs)):
+        terms = []
+        for a, others in gbar[gi]:
+            prod = " * ".join("G%d" % k for k in others)
+            terms.append("R(xi[%d])" % a + (" * " + prod if prod else ""))
+        L.append(ind + "const R Gb%d = %s;" % (gi, " + ".join(terms) if terms else "R(0)"))
+    # node adjoints
+    adj = defaultdict(list)          # (node, comp index) -> list of expressions
+    for gi, roots in enumerate(lv.roots):
+        for w, node in roots:
+            adj[(node, 0)].append("Gb%d" % gi if w == 1 else "R(%d) * Gb%d" % (w, gi))
+    dcontrib = defaultdict(list)     # M component -> expressions
+
+    def flush(n):
+        """Emit the adjoint of node n; return variable names per component."""
+        key, rank = dag.nodes[n]
+        names = []
+        for ki in range(n_sym(rank)):
+            ex = adj.get((n, ki))
+            if not ex:
+                names.append(None)
+                continue
+            nm = "b%d_%d" % (n, ki)
+            L.append(ind + "const R %s = %s;" % (nm, " + ".join(ex)))
+            names.append(nm)
+        return names
+
+    for n in range(len(dag.nodes) - 1, -1, -1):
+        key, rank = dag.nodes[n]
+        names = flush(n)
+        if all(x is None for x in names):
+            continue
+        if key[0] == "M":
+            _, mu, nu, off = key
+            for ki, K in enumerate(multi_indices(rank)):
+                if names[ki] is None:
+                    continue
+                full = (off[0] + K[0], off[1] + K[1], off[2] + K[2])
+                dcontrib[lv.comp_index[(mu, full)]].append(names[ki])
+            continue
+        _, a, b = key
+        p = dag.rank(b)
+        Ps = multi_indices(p)
+        ra = dag.rank(a)
+        # A-adjoint: Abar[K+P] += Cbar[K] * Bw[P]
+        # B-adjoint: Bbar[P] += w_P * sum_K Cbar[K] A[K+P]
+        bacc = defaultdict(list)
+        for ki, K in enumerate(multi_indices(rank)):
+            if names[ki] is None:
+                continue
+            for j, P in enumerate(Ps):
+                full = (K[0] + P[0], K[1] + P[1], K[2] + P[2])
+                if dag.nodes[a][0][0] == "M" or True:
+                    aidx = multi_indices(ra).index(full)
+                    adj[(a, aidx)].append("%s * %s" % (names[ki], wname[n][j]))
+                bacc[j].append((names[ki], comp_ref(a, full)))
+        for j, lst in bacc.items():
+            P = Ps[j]
+            w = multinomial_weight(P)
+            nm = "c%d_%d" % (n, j)
+            L.append(ind + "R %s = %s * %s;" % (nm, lst[0][0], lst[0][1]))
+            for x, y in lst[1:]:
+                L.append(ind + "%s = fmadd(%s, %s, %s);" % (nm, x, y, nm))
+            bidx = j
+            adj[(b, bidx)].append(nm if w == 1 else "R(%d) * %s" % (w, nm))
+    for c in range(len(lv.comps)):
+        ex = dcontrib.get(c)
+        L.append(ind + "D[%d] = %s;" % (c, " + ".join(ex) if ex else "R(0)"))
+    L.append(ind + "return E;")
+    L.append("  }")
+    return L
+
+
+def emit_header(lv: Level):
+    name = "MtpLevel%d" % lv.level
+    out = []
+    out.append("// Generated by paper_2510_00193_gb300/basisgen.py for MTP level %d. Do not edit." % lv.level)
+    out.append("#pragma once")
+    out.append("#include \"mtp_math.cuh\"")
+    out.append("namespace mtp {")
+    out.append("struct %s {" % name)
+    out.append("  static constexpr int LEVEL = %d;" % lv.level)
+    out.append("  static constexpr int NMU = %d;" % lv.nmu)
+    out.append("  static constexpr int NCOMP = %d;" % len(lv.comps))
+    out.append("  static constexpr int NBASIS = %d;" % lv.m)
+    out.append("  static constexpr int NGRAPH = %d;" % len(lv.graphs))
+    out.append("  static constexpr int NUMAX = %d;" % max(lv.nu_max))
+    out += emit_moments(lv)
+    out += emit_pair_adjoint(lv)
+    out += emit_contract(lv)
+    out.append("};")
+    out.append("}  // namespace mtp")
+    return "\n".join(out) + "\n"
+
+
+def emit_tables(levels):
+    """Host tables: per level the basis functions as factor lists of graphs,
+    graphs as (nv, mu[], e[]), and each graph's expanded polynomial."""
+    out = ["// Generated by paper_2510_00193_gb300/basisgen.py. Do not edit.", "#pragma once",
+           "#include <cstdint>", "namespace mtp { namespace tables {"]
+    entries = []
+    for lv in levels:
+        L = lv.level
+        gdata = []
+        for g in lv.graphs:
+            gdata += [g.nv] + list(g.mu) + list(g.e)
+        bdata = []
+        for b in lv.bases:
+            bdata += [len(b)] + list(b)
+        pdata = []
+        nterms = 0
+        for g in lv.graphs:
+            poly = sorted(expand_graph(g).items())
+            pdata.append(len(poly))
+            for mono, coef in poly:
+                pdata.append(coef)
+                for mu, K in mono:
+                    pdata += [mu, K[0], K[1], K[2]]
+                nterms += 1
+        cdata = []
+        for mu, K in lv.comps:
+            cdata += [mu, K[0], K[1], K[2]]
+        for nm, arr in (("graphs", gdata), ("bases", bdata), ("poly", pdata), ("comps", cdata)):
+            out.append("static const int64_t L%d_%s[] = {%s};" % (L, nm, ",".join(str(v) for v in arr) or "0"))
+        entries.append("  {%d, %d, %d, %d, %d, L%d_graphs, %d, L%d_bases, %d, L%d_poly, %d, L%d_comps, %d, %d}" % (
+            L, lv.nmu, lv.m, len(lv.graphs), len(lv.comps), L, len(gdata), L, len(bdata), L, len(pdata), L,
+            len(cdata), lv.n_enumerated))
+    out.append("struct LevelTable { int level, nmu, m, ngraph, ncomp; const int64_t* graphs; int64_t ngraphs_len;"
+               " const int64_t* bases; int64_t nbases_len; const int64_t* poly; int64_t npoly_len;"
+               " const int64_t* comps; int64_t ncomps_len; int n_enumerated; };")
+    out.append("static const LevelTable kLevels[] = {")
+    out.append(",\n".join(entries))
+    out.append("};")
+    out.append("static const int kNumLevels = %d;" % len(levels))
+    out.append("}}  // namespace mtp::tables")
+    return "\n".join(out) + "\n"
+
+
+LEVELS = (2, 4, 6, 8, 10, 12, 14, 16, 18, 20)
+
+
+def generate(outdir, levels=LEVELS):
+    os.makedirs(outdir, exist_ok=True)
+    lvs = [Level(L) for L in levels]
+    written = []
+    for lv in lvs:
+        path = os.path.join(outdir, "mtp_level%d.cuh" % lv.level)
+        _write_if_changed(path, emit_header(lv))
+        written.append(path)
+    path = os.path.join(outdir, "mtp_tables.h")
+    _write_if_changed(path, emit_tables(lvs))
+    written.append(path)
+    return written
+
+
+def _write_if_changed(path, text):
+    if os.path.exists(path):
+        with open(path) as fh:
+            if fh.read() == text:
+                return
+    with open(path, "w") as fh:
+        fh.write(text)
+
+
+if __name__ == "__main__":
+    lv = [int(a) for a in sys.argv[2:]] or list(LEVELS)
+    generate(sys.argv[1], lv)

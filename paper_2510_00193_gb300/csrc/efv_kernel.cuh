@@ -1,0 +1,328 @@
+// Energy / force / virial / parameter-gradient kernel for one MTP level.
+//
+// One thread per centre atom i, two sweeps over its neighbours:
+//   sweep 1: pair vector, radial functions f_mu (Chebyshev basis times
+//            (R_cut - r)^2), moment components M[c] += f_mu rhat^K, all in
+//            registers (straight-line code generated per level);
+//   contraction: graph values, basis products, E_i = s + sum xi B and the
+//            reverse pass D = dE_i/dM (generated straight-line code);
+//   sweep 2: per pair g_ij = dE_i/dr_ij from D (generated), F_i += g,
+//            F_j -= g (FP64 atomics), W -= sym(g (x) r_ij), and with DTHETA
+//            dE/dc[mu][k][zi][zj] += Q_k(r) S_mu.
+// Reductions of E, W and dE/dtheta are FP64 (warp shuffles, then one atomic
+// per block).
+#pragma once
+#include <cuda_runtime.h>
+
+#include "mtp_internal.cuh"
+#include "mtp_math.cuh"
+
+namespace mtp {
+
+constexpr int kEfvThreads = 128;
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  return v;
+}
+
+__device__ __forceinline__ void flag_status(int* status, int code) {
+  if (status) atomicCAS(status, 0, code);
+}
+
+// Pair vector r_ij = x_j + n.H - x_i.
+template <class R> struct PairGeom;
+
+template <> struct PairGeom<double> {
+  // FP64: positions directly, shift s = (n1 a + n2 b) + n3 c.
+  double xi, yi, zi;
+  __device__ __forceinline__ void load_centre(const EfvArgs& a, int64_t i) {
+    xi = a.x[3 * i]; yi = a.x[3 * i + 1]; zi = a.x[3 * i + 2];
+  }
+  __device__ __forceinline__ int species_of(const EfvArgs& a, int32_t j) const { return __ldg(a.z + j); }
+  __device__ __forceinline__ void vec(const EfvArgs& a, int32_t j, int32_t img, double& dx, double& dy,
+                                      double& dz) const {
+    int n1, n2, n3;
+    unpack_image(img, n1, n2, n3);
+    const double* c = a.cell;
+    const double sx = ((double)n1 * c[0] + (double)n2 * c[3]) + (double)n3 * c[6];
+    const double sy = ((double)n1 * c[1] + (double)n2 * c[4]) + (double)n3 * c[7];
+    const double sz = ((double)n1 * c[2] + (double)n2 * c[5]) + (double)n3 * c[8];
+    dx = (__ldg(a.x + 3 * j) + sx) - xi;
+    dy = (__ldg(a.x + 3 * j + 1) + sy) - yi;
+    dz = (__ldg(a.x + 3 * j + 2) + sz) - zi;
+  }
+};
+
+template <> struct PairGeom<float> {
+  // Mixed: exact integer difference of 32.32 fixed-point fractional
+  // coordinates plus the image, converted to FP32 and mapped by the cell.
+  long long qx, qy, qz;
+  __device__ __forceinline__ void load_centre(const EfvArgs& a, int64_t i) {
+    const longlong2 p = *reinterpret_cast<const longlong2*>(a.xq + 4 * i);
+    qx = p.x; qy = p.y;
+    qz = a.xq[4 * i + 2];
+  }
+  __device__ __forceinline__ int species_of(const EfvArgs& a, int32_t j) const {
+    return (int)__ldg(a.xq + 4 * (int64_t)j + 3);
+  }
+  __device__ __forceinline__ void vec(const EfvArgs& a, int32_t j, int32_t img, float& dx, float& dy,
+                                      float& dz) const {
+    int n1, n2, n3;
+    unpack_image(img, n1, n2, n3);
+    const longlong2 p = __ldg(reinterpret_cast<const longlong2*>(a.xq + 4 * (int64_t)j));
+    const long long pz = __ldg(a.xq + 4 * (int64_t)j + 2);
+    const float s = 2.3283064365386963e-10f;  // 2^-32
+    const float fx = __ll2float_rn(p.x - qx + ((long long)n1 << 32)) * s;
+    const float fy = __ll2float_rn(p.y - qy + ((long long)n2 << 32)) * s;
+    const float fz = __ll2float_rn(pz - qz + ((long long)n3 << 32)) * s;
+    const float* c = a.cellf;
+    dx = fmaf(fz, c[6], fmaf(fy, c[3], fx * c[0]));
+    dy = fmaf(fz, c[7], fmaf(fy, c[4], fx * c[1]));
+    dz = fmaf(fz, c[8], fmaf(fy, c[5], fx * c[2]));
+  }
+};
+
+__device__ __forceinline__ float rsqrt_r(float v) { return rsqrtf(v); }
+__device__ __forceinline__ double rsqrt_r(double v) { return rsqrt(v); }
+
+// Radial functions of one pair.  c points at the (zi, zj) block, [mu][k].
+// f_mu = cut^2 sum_k c T_k, df_mu/dr = scale cut^2 sum_k c T'_k - 2 cut sum_k c T_k,
+// with T_k(xi) the Chebyshev polynomials, xi = (r - mid) scale, cut = R_cut - r.
+template <class R, int NMU, bool DERIV, bool WANT_Q>
+__device__ __forceinline__ void radial(const R* __restrict__ c, int nq, R r, R mid, R scale, R rcut, R* f,
+                                       R* df, R* q) {
+  const R x = (r - mid) * scale;
+  const R cut = rcut - r;
+  const R cut2 = cut * cut;
+  R t0 = R(1), t1 = x, d0 = R(0), d1 = R(1);
+  R A[NMU], Bd[NMU];
+#pragma unroll
+  for (int mu = 0; mu < NMU; ++mu) {
+    A[mu] = c[mu * nq];
+    Bd[mu] = R(0);
+  }
+  if (WANT_Q) q[0] = cut2;
+  if (nq > 1) {
+#pragma unroll
+    for (int mu = 0; mu < NMU; ++mu) {
+      A[mu] = fmadd(c[mu * nq + 1], x, A[mu]);
+      if (DERIV) Bd[mu] = c[mu * nq + 1];
+    }
+    if (WANT_Q) q[1] = x * cut2;
+  }
+#pragma unroll
+  for (int k = 2; k < kMaxQ; ++k) {
+    if (k < nq) {
+      const R t2 = fmadd(R(2) * x, t1, -t0);
+      const R d2 = fmadd(R(2) * x, d1, fmadd(R(2), t1, -d0));
+#pragma unroll
+      for (int mu = 0; mu < NMU; ++mu) {
+        const R cc = c[mu * nq + k];
+        A[mu] = fmadd(cc, t2, A[mu]);
+        if (DERIV) Bd[mu] = fmadd(cc, d2, Bd[mu]);
+      }
+      if (WANT_Q) q[k] = t2 * cut2;
+      t0 = t1; t1 = t2; d0 = d1; d1 = d2;
+    }
+  }
+#pragma unroll
+  for (int mu = 0; mu < NMU; ++mu) {
+    f[mu] = cut2 * A[mu];
+    if (DERIV) df[mu] = fmadd(scale * cut2, Bd[mu], R(-2) * cut * A[mu]);
+  }
+}
+
+template <class LV, class R, bool DTHETA>
+__global__ void __launch_bounds__(kEfvThreads) efv_kernel(const EfvArgs a) {
+  constexpr int NMU = LV::NMU;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int S = a.n_species;
+  const int SS = S * S;
+  const int nq = a.n_q;
+  const int cstride = (NMU * nq) | 1;  // odd stride: species-pair blocks fall on distinct banks
+  R* s_c = reinterpret_cast<R*>(smem_raw);
+  R* s_xi = s_c + SS * cstride;
+  R* s_dc = s_xi + a.m;                 // DTHETA: [SS][NMU][nq]
+  R* s_dxi = s_dc + (DTHETA ? SS * NMU * nq : 0);
+  double* s_red = reinterpret_cast<double*>(s_dxi + (DTHETA ? a.m : 0));  // 8 doubles per warp
+  int* s_cnt = reinterpret_cast<int*>(s_red + 8 * (kEfvThreads / 32));
+
+  const R* radial_src = nullptr;
+  const R* xi_src = nullptr;
+  if constexpr (sizeof(R) == 8) {
+    radial_src = reinterpret_cast<const R*>(a.radial_d);
+    xi_src = reinterpret_cast<const R*>(a.xi_d);
+  } else {
+    radial_src = reinterpret_cast<const R*>(a.radial_f);
+    xi_src = reinterpret_cast<const R*>(a.xi_f);
+  }
+  for (int t = threadIdx.x; t < NMU * nq * SS; t += blockDim.x) {
+    // global layout [mu][k][zi][zj] -> shared [zi*S+zj][mu][k]
+    const int p = t % SS;
+    const int mk = t / SS;
+    s_c[p * cstride + mk] = radial_src[t];
+  }
+  for (int t = threadIdx.x; t < a.m; t += blockDim.x) s_xi[t] = xi_src[t];
+  if (DTHETA) {
+    for (int t = threadIdx.x; t < SS * NMU * nq; t += blockDim.x) s_dc[t] = R(0);
+    for (int t = threadIdx.x; t < a.m; t += blockDim.x) s_dxi[t] = R(0);
+    for (int t = threadIdx.x; t < S; t += blockDim.x) s_cnt[t] = 0;
+  }
+  __syncthreads();
+
+  const R rcut = R(a.r_cut);
+  const R mid = R(0.5 * (a.r_min + a.r_cut));
+  const R scale = R(2.0 / (a.r_cut - a.r_min));
+  const int64_t i = a.atom_begin + (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const bool active = i < a.atom_end;
+
+  double e_i = 0.0;
+  R w[6] = {R(0), R(0), R(0), R(0), R(0), R(0)};
+  R Bv[DTHETA ? LV::NBASIS : 1];
+#pragma unroll
+  for (int t = 0; t < (DTHETA ? LV::NBASIS : 1); ++t) Bv[t] = R(0);
+
+  if (active) {
+    PairGeom<R> geom;
+    geom.load_centre(a, i);
+    const int zi = __ldg(a.z + i);
+    const int64_t beg = __ldg(a.offsets + i), end = __ldg(a.offsets + i + 1);
+    R M[LV::NCOMP];
+#pragma unroll
+    for (int c = 0; c < LV::NCOMP; ++c) M[c] = R(0);
+    for (int64_t k = beg; k < end; ++k) {
+      const int32_t j = __ldg(a.nbr_j + k);
+      const int32_t img = __ldg(a.nbr_img + k);
+      const int zj = geom.species_of(a, j);
+      R dx, dy, dz;
+      geom.vec(a, j, img, dx, dy, dz);
+      const R r2 = fmadd(dz, dz, fmadd(dy, dy, dx * dx));
+      const R rinv = rsqrt_r(r2);
+      const R r = r2 * rinv;
+      R f[NMU];
+      radial<R, NMU, false, false>(s_c + (zi * S + zj) * cstride, nq, r, mid, scale, rcut, f, nullptr, nullptr);
+      LV::template moments<R>(M, f, dx * rinv, dy * rinv, dz * rinv);
+    }
+    R D[LV::NCOMP];
+    const R ei = LV::template contract<R, DTHETA>(M, s_xi, D, Bv);
+    e_i = a.species_energy[zi] + (double)ei;
+    a.e_atom[i] = e_i;
+
+    R fx = R(0), fy = R(0), fz = R(0);
+    for (int64_t k = beg; k < end; ++k) {
+      const int32_t j = __ldg(a.nbr_j + k);
+      const int32_t img = __ldg(a.nbr_img + k);
+      const int zj = geom.species_of(a, j);
+      R dx, dy, dz;
+      geom.vec(a, j, img, dx, dy, dz);
+      const R r2 = fmadd(dz, dz, fmadd(dy, dy, dx * dx));
+      const R rinv = rsqrt_r(r2);
+      const R r = r2 * rinv;
+      R f[NMU], df[NMU], q[DTHETA ? kMaxQ : 1];
+      const R* cblk = s_c + (zi * S + zj) * cstride;
+      radial<R, NMU, true, DTHETA>(cblk, nq, r, mid, scale, rcut, f, df, q);
+      R gx, gy, gz, Smu[NMU];
+      LV::template pair_adjoint<R>(D, f, df, dx * rinv, dy * rinv, dz * rinv, rinv, gx, gy, gz, Smu);
+      fx += gx; fy += gy; fz += gz;
+      atomicAdd(a.forces + 3 * (int64_t)j, -(double)gx);
+      atomicAdd(a.forces + 3 * (int64_t)j + 1, -(double)gy);
+      atomicAdd(a.forces + 3 * (int64_t)j + 2, -(double)gz);
+      w[0] = fmadd(-gx, dx, w[0]);
+      w[1] = fmadd(-gy, dy, w[1]);
+      w[2] = fmadd(-gz, dz, w[2]);
+      w[3] = fmadd(R(-0.5), fmadd(gx, dy, gy * dx), w[3]);
+      w[4] = fmadd(R(-0.5), fmadd(gx, dz, gz * dx), w[4]);
+      w[5] = fmadd(R(-0.5), fmadd(gy, dz, gz * dy), w[5]);
+      if (DTHETA) {
+        R* dst = s_dc + (zi * S + zj) * NMU * nq;
+#pragma unroll
+        for (int mu = 0; mu < NMU; ++mu) {
+#pragma unroll
+          for (int kk = 0; kk < kMaxQ; ++kk)
+            if (kk < nq) atomicAdd(dst + mu * nq + kk, q[kk] * Smu[mu]);
+        }
+      }
+    }
+    atomicAdd(a.forces + 3 * i, (double)fx);
+    atomicAdd(a.forces + 3 * i + 1, (double)fy);
+    atomicAdd(a.forces + 3 * i + 2, (double)fz);
+    if (!isfinite(e_i) || !isfinite((double)fx) || !isfinite((double)fy) || !isfinite((double)fz))
+      flag_status(a.status, MTP_ERR_NONFINITE);
+    if (DTHETA) atomicAdd(s_cnt + zi, 1);
+  }
+
+  // FP64 block reductions: energy and virial.
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  double vals[7] = {e_i, (double)w[0], (double)w[1], (double)w[2], (double)w[3], (double)w[4], (double)w[5]};
+#pragma unroll
+  for (int t = 0; t < 7; ++t) vals[t] = warp_sum(vals[t]);
+  if (lane == 0) {
+#pragma unroll
+    for (int t = 0; t < 7; ++t) s_red[warp * 8 + t] = vals[t];
+  }
+  if (DTHETA) {
+#pragma unroll
+    for (int t = 0; t < (DTHETA ? LV::NBASIS : 1); ++t) {
+      const double v = warp_sum((double)Bv[t]);
+      if (lane == 0) atomicAdd(s_dxi + t, R(v));
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x < 7) {
+    double acc = 0.0;
+    for (int wi = 0; wi < kEfvThreads / 32; ++wi) acc += s_red[wi * 8 + threadIdx.x];
+    if (threadIdx.x == 0) atomicAdd(a.e_total, acc);
+    else atomicAdd(a.virial + threadIdx.x - 1, acc);
+  }
+  if (DTHETA) {
+    // theta = [ s (S) | c [mu][k][zi][zj] | xi (m) ]
+    for (int t = threadIdx.x; t < S; t += blockDim.x) atomicAdd(a.dtheta + t, (double)s_cnt[t]);
+    for (int t = threadIdx.x; t < SS * NMU * nq; t += blockDim.x) {
+      const int p = t / (NMU * nq);
+      const int mk = t % (NMU * nq);
+      atomicAdd(a.dtheta + S + (int64_t)mk * SS + p, (double)s_dc[t]);
+    }
+    for (int t = threadIdx.x; t < a.m; t += blockDim.x)
+      atomicAdd(a.dtheta + S + (int64_t)NMU * nq * SS + t, (double)s_dxi[t]);
+  }
+}
+
+template <class LV, class R, bool DTHETA>
+int efv_launch_typed(const EfvArgs& a, cudaStream_t stream) {
+  const int SS = a.n_species * a.n_species;
+  const int cstride = (LV::NMU * a.n_q) | 1;
+  size_t bytes = sizeof(R) * ((size_t)SS * cstride + a.m);
+  if (DTHETA) bytes += sizeof(R) * ((size_t)SS * LV::NMU * a.n_q + a.m);
+  bytes = (bytes + 15) & ~size_t(15);
+  bytes += sizeof(double) * 8 * (kEfvThreads / 32) + sizeof(int) * kMaxSpecies;
+  auto kern = efv_kernel<LV, R, DTHETA>;
+  if (bytes > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    if (e != cudaSuccess) {
+      set_error("cudaFuncSetAttribute: %s", cudaGetErrorString(e));
+      return MTP_ERR_CUDA;
+    }
+  }
+  const int64_t n = a.atom_end - a.atom_begin;
+  if (n <= 0) return MTP_OK;
+  const unsigned grid = (unsigned)((n + kEfvThreads - 1) / kEfvThreads);
+  kern<<<grid, kEfvThreads, bytes, stream>>>(a);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) {
+    set_error("efv kernel launch (level %d): %s", LV::LEVEL, cudaGetErrorString(e));
+    return MTP_ERR_CUDA;
+  }
+  return MTP_OK;
+}
+
+template <class LV>
+int efv_launch(const EfvArgs& a, int precision, bool want_dtheta, cudaStream_t stream) {
+  if (precision == MTP_MIXED) {
+    return want_dtheta ? efv_launch_typed<LV, float, true>(a, stream) : efv_launch_typed<LV, float, false>(a, stream);
+  }
+  return want_dtheta ? efv_launch_typed<LV, double, true>(a, stream) : efv_launch_typed<LV, double, false>(a, stream);
+}
+
+}  // namespace mtp

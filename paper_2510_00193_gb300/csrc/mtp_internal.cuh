@@ -1,0 +1,104 @@
+// Internal definitions of the GB300 MTP library (not part of the C-ABI).
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <vector>
+
+#include "mtp.h"
+
+namespace mtp {
+
+void set_error(const char* fmt, ...);
+
+#define MTP_TRY_CUDA(call)                                                                      \
+  do {                                                                                          \
+    cudaError_t e_ = (call);                                                                    \
+    if (e_ != cudaSuccess) {                                                                    \
+      mtp::set_error("%s failed: %s (%s:%d)", #call, cudaGetErrorString(e_), __FILE__, __LINE__); \
+      return e_ == cudaErrorMemoryAllocation ? MTP_ERR_OOM : MTP_ERR_CUDA;                      \
+    }                                                                                           \
+  } while (0)
+
+// Device buffer that only grows.
+struct DevBuf {
+  void* ptr = nullptr;
+  size_t bytes = 0;
+  int ensure(size_t want);
+  void release();
+  template <class T> T* as() const { return static_cast<T*>(ptr); }
+};
+
+constexpr int kMaxSpecies = 16;
+constexpr int kMaxQ = 16;
+constexpr int kImageBias = 512;  // image components are stored as n + 512 in 10 bits each
+
+__host__ __device__ inline int32_t pack_image(int n1, int n2, int n3) {
+  return (int32_t)(((uint32_t)(n1 + kImageBias)) | ((uint32_t)(n2 + kImageBias) << 10) |
+                   ((uint32_t)(n3 + kImageBias) << 20));
+}
+__host__ __device__ inline void unpack_image(int32_t p, int& n1, int& n2, int& n3) {
+  uint32_t u = (uint32_t)p;
+  n1 = (int)(u & 1023u) - kImageBias;
+  n2 = (int)((u >> 10) & 1023u) - kImageBias;
+  n3 = (int)((u >> 20) & 1023u) - kImageBias;
+}
+
+// Everything an energy/force launch needs, passed by value.
+struct EfvArgs {
+  int64_t atom_begin, atom_end, n_atoms;
+  const int64_t* offsets;
+  const int32_t* nbr_j;
+  const int32_t* nbr_img;
+  const double* x;          // FP64 path
+  const long long* xq;      // mixed path: 32.32 fixed-point fractional coordinates [N][3]
+  const int32_t* z;
+  double cell[9];
+  float cellf[9];
+  int n_species, n_q, n_mu, m;
+  double r_min, r_cut;
+  const double* species_energy;
+  const double* radial_d;   // [n_mu][n_q][S][S]
+  const double* xi_d;
+  const float* radial_f;
+  const float* xi_f;
+  double* e_atom;
+  double* forces;
+  double* virial;
+  double* e_total;
+  double* dtheta;           // nullable
+  int* status;
+};
+
+using EfvLaunch = int (*)(const EfvArgs&, int precision, bool want_dtheta, cudaStream_t);
+
+struct LevelEntry {
+  int level;
+  EfvLaunch efv;
+  int shmem_bytes_max;
+};
+
+const LevelEntry* find_level(int level);
+
+}  // namespace mtp
+
+struct mtp_handle {
+  int device = 0;
+  int level = 0, n_species = 0, n_q = 0, n_mu = 0, m = 0, n_comp = 0;
+  double r_min = 0, r_cut = 0;
+  int64_t n_params = 0;
+  const mtp::LevelEntry* ops = nullptr;
+  std::vector<double> h_species, h_radial, h_xi;
+  mtp::DevBuf species, radial_d, xi_d, radial_f, xi_f, status;
+  mtp::DevBuf xq;        // fixed-point positions scratch
+};
+
+struct mtp_nlist {
+  int device = 0;
+  int64_t n_atoms = 0, n_pairs = 0;
+  double r_cut = 0;
+  double cell[9] = {0};
+  int pbc[3] = {0, 0, 0};
+  mtp::DevBuf offsets, nbr_j, nbr_img;
+  mtp::DevBuf counts, bins, bin_start, bin_atoms, wrapped, status;
+};
