@@ -1,0 +1,322 @@
+"""Benchmark: MTP energy + force evaluation on the 1,024,000-atom level-16 BCC
+workload (3 species, r_cut 5.0 A, ~26 neighbours per atom), FP32-mixed, one
+GPU.  Prints one JSON line.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+A step is one mtp_compute_efv call (site energies, forces, virial) on the
+prebuilt neighbour list; the neighbour build is timed separately and reported
+as nbr_build_ms.  With N > 1 (torchrun) every rank evaluates its own replica of
+the workload (independent configurations, no exchange) and the value is the sum.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "MTP E+F atom-steps/s, 1M atoms lev16, FP32-mixed vs FP64; % HBM roofline"
+UNIT = "atom-steps/s"
+WORKLOAD = "bcc-80x80x80 (1,024,000 atoms), MTP level 16, 3 species, n_q 8, r_cut 5.0 A, sigma 0.08 A"
+POTENTIAL = "bcc-l16-s3"
+CELLS = (80, 80, 80)
+SM_COUNT = 152
+FP32_LANES = 128
+
+
+def _peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as fh:
+            d = json.load(fh)
+        return d.get("hbm_gbs", 6800.0), d.get("sm_max_mhz", 2070.0), "measured"
+    return 6800.0, 2070.0, "fallback"
+
+
+def _dist():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    return rank, world
+
+
+def _workload(cells=CELLS):
+    import synth
+    return synth.crystal("bcc", tuple(cells), 3.16, 0.08, 3, 2)
+
+
+def _flops_per_atom(level, n_q, n_mu, nbar):
+    """Algorithmic FP32 flops per atom of one E+F evaluation (geometry, radial
+    functions and derivatives, monomials, moments, contraction and its reverse,
+    pair adjoint, force/virial accumulation), counted from the generated code.
+    Recomputation in the second neighbour sweep is not counted."""
+    sys.path.insert(0, os.path.join(ROOT, "paper_2510_00193_gb300"))
+    import basisgen
+    fc = basisgen.flop_counts(basisgen.Level(level))
+    q = n_q
+    radial_f = 4 + 2 * n_mu + (q - 2) * (3 + 2 * n_mu) + n_mu
+    radial_d = (q - 2) * (4 + 2 * n_mu) + 1 + 4 * n_mu
+    geom, accum = 28, 24
+    per_pair = geom + radial_f + fc["monomials"] + fc["moments"] + radial_d + fc["pair_adjoint"] + accum
+    return per_pair * nbar + fc["contract"], fc
+
+
+class ClockSampler:
+    """nvidia-smi clock and throttle samples while the timed region runs."""
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", "clocks_bench.csv") if os.path.isdir(
+            os.path.join(ROOT, "gpurun_out")) else "/tmp/clocks_bench.csv"
+
+    def __enter__(self):
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + q,
+                                          "--format=csv,noheader,nounits", "-lms", "100"], stdout=self.fh,
+                                         stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+            self.fh.close()
+
+    def summary(self):
+        if self.proc is None or not os.path.exists(self.path):
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        rows = []
+        with open(self.path) as fh:
+            for line in fh:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k].lower().startswith("active")})
+        loaded = sorted(sm)[len(sm) // 2:] if sm else []
+        return {"sm_mhz": statistics.median(loaded) if loaded else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def oracle_rate(st, n_sample, seed=3):
+    """Oracle E+F throughput on a bounded sample of centre atoms."""
+    import numpy as np
+    import torch
+
+    from oracle import mtp as O
+    from tests.helpers import min_image_candidates, pot_dict
+
+    model = O.load_model(pot_dict(POTENTIAL))
+    g = np.random.default_rng(seed)
+    centres = np.sort(g.choice(st.n, n_sample, replace=False))
+    cand = min_image_candidates(st, centres, 5.5)
+    t0 = time.perf_counter()
+    nl = O.neighbor_list(st.x, st.cell, st.pbc, 5.0, query=centres, candidates=cand)
+    O.evaluate(model, st.x, st.z, st.cell, nl, want=("e", "f", "w"), atoms=centres)
+    dt = time.perf_counter() - t0
+    return n_sample / dt, dt, torch.get_num_threads()
+
+
+def run_reference(args):
+    rank, world = _dist()
+    if rank != 0:
+        return
+    st = _workload()
+    rates = []
+    n_sample = 48
+    for _ in range(args.warmup):
+        oracle_rate(st, 8)
+    t_total = 0.0
+    for k in range(args.steps):
+        r, dt, threads = oracle_rate(st, n_sample, seed=100 + k)
+        rates.append(r)
+        t_total += dt
+    value = n_sample * args.steps / t_total
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t_total / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "precision": "fp64 (oracle)"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
+                         "sample": "%d random centre atoms of the workload per step (E_i and their force and "
+                                   "virial contributions)" % n_sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    import paper_2510_00193_gb300 as P
+
+    rank, world = _dist()
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    st = _workload((args.cells,) * 3)
+    pot = P.Potential.from_file(os.path.join(ROOT, "potentials", POTENTIAL + ".json"))
+    x = torch.tensor(st.x, dtype=torch.float64, device="cuda")
+    z = torch.tensor(st.z, dtype=torch.int32, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    # neighbour list (timed separately)
+    nl = P.mtp_build_neighbors(pot, x, st.cell, st.pbc)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    nl = P.mtp_build_neighbors(pot, x, st.cell, st.pbc, nlist=nl)
+    torch.cuda.synchronize()
+    nbr_ms = 1e3 * (time.perf_counter() - t0)
+    n_atoms, n_pairs = nl.info()
+    nbar = n_pairs / n_atoms
+
+    def timed(precision, steps, warmup):
+        out = P.mtp_compute_efv(pot, nl, x, z, st.cell, precision=precision)
+        for _ in range(warmup):
+            P.mtp_compute_efv(pot, nl, x, z, st.cell, precision=precision, out=out)
+        torch.cuda.synchronize()
+        if world > 1:
+            torch.distributed.barrier()
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(steps + 1)]
+        ev[0].record(stream)
+        for k in range(steps):
+            P.mtp_compute_efv(pot, nl, x, z, st.cell, precision=precision, out=out)
+            ev[k + 1].record(stream)
+        torch.cuda.synchronize()
+        per = [ev[k].elapsed_time(ev[k + 1]) for k in range(steps)]
+        return out, per
+
+    with ClockSampler(local) as clk:
+        out, per = timed(P.MTP_MIXED, args.steps, args.warmup)
+    clocks = clk.summary()
+    ms = sum(per) / len(per)
+    if world > 1:
+        t = torch.tensor([ms], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = t.item()
+    value = world * n_atoms / (ms * 1e-3)
+
+    # FP64 path for the mixed/FP64 ratio (a few steps)
+    ms64 = None
+    if not args.no_fp64:
+        _, per64 = timed(P.MTP_FP64, max(2, min(3, args.steps)), 1)
+        ms64 = sum(per64) / len(per64)
+
+    # end to end through the public API: pinned host positions in, forces and energy out
+    xh = torch.tensor(st.x, dtype=torch.float64).pin_memory()
+    zh = torch.tensor(st.z, dtype=torch.int32).pin_memory()
+    fh = torch.empty((n_atoms, 3), dtype=torch.float64).pin_memory()
+    eh = torch.empty(1, dtype=torch.float64).pin_memory()
+    xd = torch.empty_like(x)
+    zd = torch.empty_like(z)
+    e2e_steps = 0 if args.no_e2e else args.steps
+    for k in range(args.warmup + e2e_steps):
+        if k == args.warmup:
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+        xd.copy_(xh, non_blocking=True)
+        zd.copy_(zh, non_blocking=True)
+        o = P.mtp_compute_efv(pot, nl, xd, zd, st.cell, precision=P.MTP_MIXED, out=out)
+        fh.copy_(o["forces"], non_blocking=True)
+        eh.copy_(o["e_total"], non_blocking=True)
+    e2e_ms = None
+    if e2e_steps:
+        e1.record(stream)
+        torch.cuda.synchronize()
+        e2e_ms = e0.elapsed_time(e1) / e2e_steps
+    h2d = xh.numel() * 8 + zh.numel() * 4
+    d2h = fh.numel() * 8 + 8
+
+    hbm_gbs, max_mhz, peak_src = _peaks()
+    flops_atom, fc = _flops_per_atom(pot.level, pot.n_q, pot.n_mu, nbar)
+    mhz = max_mhz
+    peak_tflops = SM_COUNT * FP32_LANES * 2 * mhz * 1e6 / 1e12
+    achieved_tflops = flops_atom * n_atoms / (ms * 1e-3) / 1e12
+    bytes_atom = 16 + 8 * nbar + 24 + 8      # fixed-point position, (j, image) per pair, force, site energy
+    hbm_achieved = bytes_atom * n_atoms / (ms * 1e-3) / 1e9
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        r, dt, threads = oracle_rate(st, args.cpu_sample)
+        cpu = {"value": r, "unit": UNIT, "cores": threads, "kind": "oracle",
+               "sample": "%d random centre atoms of the workload (E_i with their force and virial "
+                         "contributions), %.1f s" % (args.cpu_sample, dt)}
+    if rank == 0:
+        workload = WORKLOAD if args.cells == CELLS[0] else WORKLOAD.replace("80x80x80 (1,024,000", "%dx%dx%d (%d" % (
+            args.cells, args.cells, args.cells, n_atoms))
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": workload, "precision": "mixed (FP32 arithmetic, FP64 accumulation)",
+                       "l2": "inputs larger than L2 (neighbour list %.0f MB)" % (n_pairs * 8 / 1e6),
+                       "parallelism": "replicas" if world > 1 else "single GPU",
+                       "mean_neighbours": round(nbar, 3)},
+            "fp64": ({"value": world * n_atoms / (ms64 * 1e-3), "unit": UNIT, "ms_per_step": ms64}
+                     if ms64 else None),
+            "mixed_over_fp64": (ms64 / ms) if ms64 else None,
+            "nbr_build_ms": nbr_ms,
+            "roofline": {"bound": "alu", "achieved": achieved_tflops, "peak": peak_tflops, "unit": "TFLOP/s",
+                         "frac": achieved_tflops / peak_tflops, "traffic": None,
+                         "peak_source": "152 SMs x 128 FP32 lanes x 2 flop x %.0f MHz (max SM clock)" % mhz,
+                         "flops_per_atom": flops_atom},
+            "hbm": {"achieved": hbm_achieved, "peak": hbm_gbs, "unit": "GB/s", "frac": hbm_achieved / hbm_gbs,
+                    "bytes_per_atom": bytes_atom, "peak_source": peak_src},
+            "cpu_baseline": cpu,
+            "e2e": ({"value": world * n_atoms / (e2e_ms * 1e-3), "unit": UNIT, "h2d_bytes_per_step": h2d,
+                     "d2h_bytes_per_step": d2h} if e2e_ms else None),
+            "gpu_launches": 2 * args.steps,
+            "clocks": clocks,
+        }
+        print(json.dumps(line))
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--cpu-sample", type=int, default=256)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 comparison steps")
+    ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end steps")
+    ap.add_argument("--cells", type=int, default=CELLS[0], help="BCC cells per edge (80: the 1,024,000-atom "
+                    "workload; smaller values only for profiling captures)")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

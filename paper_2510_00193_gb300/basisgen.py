@@ -749,3 +749,39 @@ def _write_if_changed(path, text):
 if __name__ == "__main__":
     lv = [int(a) for a in sys.argv[2:]] or list(LEVELS)
     generate(sys.argv[1], lv)
+
+
+# ---------------------------------------------------------------------------
+# floating-point operation counts of the generated code (for roofline figures)
+# ---------------------------------------------------------------------------
+
+
+def _flops_of(lines):
+    """fmadd = 2 flops, every other binary * + - = 1 flop (integer constants
+    folded into R(k) * x count as one multiply)."""
+    import re
+    total = 0
+    for ln in lines:
+        code = ln.split("//")[0]
+        if "=" not in code or code.strip().startswith(("template", "__device__", "}", "(void)", "if (WANT_B)")):
+            continue
+        rhs = code.split("=", 1)[1]
+        total += 2 * rhs.count("fmadd(")
+        total += len(re.findall(r"[^\s(,]\s*[\*\+\-]\s*[^\s)]", rhs.replace("fmadd(", "(")))
+    return total
+
+
+def flop_counts(lv):
+    """Per-pair and per-atom flop counts of the generated functions."""
+    maxnu = max(lv.nu_max)
+    n_mono = sum(n_sym(n) for n in range(1, maxnu + 1))
+    mom = emit_moments(lv)
+    adj = emit_pair_adjoint(lv)
+    con = emit_contract(lv)
+    return {
+        "monomials": n_mono,
+        "moments": _flops_of(mom) - n_mono,
+        "pair_adjoint": _flops_of(adj) - n_mono,
+        "contract": _flops_of(con),
+        "ncomp": len(lv.comps),
+    }

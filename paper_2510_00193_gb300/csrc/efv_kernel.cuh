@@ -134,6 +134,15 @@ __device__ __forceinline__ void radial(const R* __restrict__ c, int nq, R r, R m
   }
 }
 
+// Byte offset of the FP64 reduction area in the kernel's dynamic shared memory.
+template <class R, int NMU, bool DTHETA>
+__host__ __device__ __forceinline__ size_t efv_red_offset(int SS, int nq, int m) {
+  const size_t cstride = (size_t)((NMU * nq) | 1);
+  size_t bytes = sizeof(R) * ((size_t)SS * cstride + m);
+  if (DTHETA) bytes += sizeof(R) * ((size_t)SS * NMU * nq + m);
+  return (bytes + 15) & ~size_t(15);
+}
+
 template <class LV, class R, bool DTHETA>
 __global__ void __launch_bounds__(kEfvThreads) efv_kernel(const EfvArgs a) {
   constexpr int NMU = LV::NMU;
@@ -146,7 +155,9 @@ __global__ void __launch_bounds__(kEfvThreads) efv_kernel(const EfvArgs a) {
   R* s_xi = s_c + SS * cstride;
   R* s_dc = s_xi + a.m;                 // DTHETA: [SS][NMU][nq]
   R* s_dxi = s_dc + (DTHETA ? SS * NMU * nq : 0);
-  double* s_red = reinterpret_cast<double*>(s_dxi + (DTHETA ? a.m : 0));  // 8 doubles per warp
+  // FP64 reduction scratch after the R-typed arrays, on a 16-byte boundary
+  const size_t red_off = efv_red_offset<R, NMU, DTHETA>(SS, nq, a.m);
+  double* s_red = reinterpret_cast<double*>(smem_raw + red_off);  // 8 doubles per warp
   int* s_cnt = reinterpret_cast<int*>(s_red + 8 * (kEfvThreads / 32));
 
   const R* radial_src = nullptr;
@@ -292,10 +303,7 @@ __global__ void __launch_bounds__(kEfvThreads) efv_kernel(const EfvArgs a) {
 template <class LV, class R, bool DTHETA>
 int efv_launch_typed(const EfvArgs& a, cudaStream_t stream) {
   const int SS = a.n_species * a.n_species;
-  const int cstride = (LV::NMU * a.n_q) | 1;
-  size_t bytes = sizeof(R) * ((size_t)SS * cstride + a.m);
-  if (DTHETA) bytes += sizeof(R) * ((size_t)SS * LV::NMU * a.n_q + a.m);
-  bytes = (bytes + 15) & ~size_t(15);
+  size_t bytes = efv_red_offset<R, LV::NMU, DTHETA>(SS, a.n_q, a.m);
   bytes += sizeof(double) * 8 * (kEfvThreads / 32) + sizeof(int) * kMaxSpecies;
   auto kern = efv_kernel<LV, R, DTHETA>;
   if (bytes > 48 * 1024) {
