@@ -4,9 +4,9 @@
  * The library evaluates the Moment Tensor Potential (MTP) that the paper
  * accelerates inside LAMMPS: site energies, forces, the virial (stress), the
  * parameter gradient and the active-learning extrapolation grade (paper
- * Sec. 2.1, "Inference computes energies, forces, and stresses"; Sec. 2.1 and
- * Sec. 2.3 on configuration and neighbourhood mode grades with selection and
- * break thresholds).  The model itself is the published MTP the paper cites
+ * Sec. 2.1: inference yields energies, forces and stresses; Sec. 2.1 and
+ * Sec. 2.3: configuration- and neighbourhood-mode grades with a selection and
+ * a break threshold).  The model itself is the published MTP the paper cites
  * (Shapeev 2016; MLIP-2/MLIP-3):
  *
  *   E_i = s[z_i] + sum_alpha xi_alpha B_alpha(i),  E = sum_i E_i,
@@ -123,7 +123,7 @@ void mtp_free_nlist(mtp_nlist* nl);
  * precision: MTP_FP64, or MTP_MIXED (radial basis, moments, contractions and
  * the adjoint in FP32; pair vectors from 32.32 fixed-point fractional
  * coordinates; energies, forces, virial and gradients accumulated in FP64).
- * chunk_atoms: centre atoms per launch (paper Sec. 2.3 "chunksize"); 0 = all.
+ * chunk_atoms: centre atoms per launch (the chunk size of paper Sec. 2.3); 0 = all.
  * Outputs (DEVICE, overwritten): e_atom [N], forces [N][3], virial [6],
  * e_total [1]; dEdtheta [n_params] or NULL to skip the parameter gradient. */
 int mtp_compute_efv(mtp_handle* h, const mtp_nlist* nl, const double* x_dev, const int32_t* z_dev,
