@@ -131,6 +131,23 @@ int mtp_compute_efv(mtp_handle* h, const mtp_nlist* nl, const double* x_dev, con
                     double* e_atom_dev, double* forces_dev, double* virial_dev, double* e_total_dev,
                     double* dEdtheta_dev, void* stream);
 
+/* Same evaluation as mtp_compute_efv with precision MTP_MIXED and no
+ * parameter gradient, but the call allocates no device memory: its
+ * fixed-point position scratch is a 2 MiB array built into the library, so
+ * n_atoms may be at most 65536 (larger n fails with MTP_ERR_ARG; use
+ * mtp_compute_efv then).  For callers that must not have a library allocate
+ * during a step: an MD engine that sets its whole device-memory budget at
+ * start-up, or a loop where cudaMalloc's device-wide synchronisation would
+ * stall other streams.  The paper has no counterpart; this entry point exists
+ * for such callers only.  The first call on each device looks up the scratch
+ * array's device address (cudaGetSymbolAddress, with that device current);
+ * make that first call before any stream capture starts.  All calls on a
+ * device share the scratch array, so calls that overlap on the GPU race:
+ * issue them one after another.  Arguments and outputs as mtp_compute_efv. */
+int mtp_compute_efv_noalloc(mtp_handle* h, const mtp_nlist* nl, const double* x_dev, const int32_t* z_dev,
+                            int64_t n_atoms, const double* cell, int64_t chunk_atoms, double* e_atom_dev,
+                            double* forces_dev, double* virial_dev, double* e_total_dev, void* stream);
+
 /* Device status word of the handle: the first device-side error recorded
  * since the last call (non-finite site energy or force, ...), then cleared.
  * Synchronises `stream`. */

@@ -18,7 +18,8 @@ from ._lib import MTP_FP64, MTP_MIXED, MtpError, check
 
 __all__ = [
     "MTP_FP64", "MTP_MIXED", "MtpError", "Potential", "NeighborList", "mtp_basis_info", "mtp_basis_table",
-    "mtp_load_params", "mtp_build_neighbors", "mtp_compute_efv", "mtp_device_status", "library_path",
+    "mtp_load_params", "mtp_build_neighbors", "mtp_compute_efv", "mtp_compute_efv_noalloc", "mtp_device_status",
+    "library_path",
 ]
 
 
@@ -227,6 +228,23 @@ def mtp_compute_efv(potential: Potential, nlist: NeighborList, x, z, cell, preci
         _dptr(out["e_atom"], torch.float64, n, "e_atom"), _dptr(out["forces"], torch.float64, 3 * n, "forces"),
         _dptr(out["virial"], torch.float64, 6, "virial"), _dptr(out["e_total"], torch.float64, 1, "e_total"),
         _dptr(out["dtheta"], torch.float64, potential.n_params, "dtheta") if dtheta else None, _stream_ptr(stream)))
+    return out
+
+
+def mtp_compute_efv_noalloc(potential: Potential, nlist: NeighborList, x, z, cell, out, chunk_atoms=0,
+                            stream=None) -> dict:
+    """Mixed-precision site energies, forces, virial and total energy into the
+    caller's ``out`` tensors (same keys as mtp_compute_efv), with no device
+    allocation inside the library call; at most 65536 atoms."""
+    import torch
+    n = x.shape[0]
+    c = _host_d(cell, 9)
+    check(_lib.load().mtp_compute_efv_noalloc(
+        potential.handle, nlist.handle, _dptr(x, torch.float64, 3 * n, "x"), _dptr(z, torch.int32, n, "z"), n,
+        c.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), int(chunk_atoms),
+        _dptr(out["e_atom"], torch.float64, n, "e_atom"), _dptr(out["forces"], torch.float64, 3 * n, "forces"),
+        _dptr(out["virial"], torch.float64, 6, "virial"), _dptr(out["e_total"], torch.float64, 1, "e_total"),
+        _stream_ptr(stream)))
     return out
 
 

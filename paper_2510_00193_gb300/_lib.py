@@ -59,6 +59,7 @@ SIGNATURES = {
     "mtp_nlist_copy": (ctypes.c_int, [_VP, _VP, _VP, _VP, _VP]),
     "mtp_free_nlist": (None, [_VP]),
     "mtp_compute_efv": (ctypes.c_int, [_VP, _VP, _VP, _VP, _I64, _P_D, _I32, _I64, _VP, _VP, _VP, _VP, _VP, _VP]),
+    "mtp_compute_efv_noalloc": (ctypes.c_int, [_VP, _VP, _VP, _VP, _I64, _P_D, _I64, _VP, _VP, _VP, _VP, _VP]),
     "mtp_device_status": (ctypes.c_int, [_VP, _VP]),
     "mtp_last_error": (ctypes.c_char_p, []),
 }
