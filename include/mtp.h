@@ -133,7 +133,8 @@ int mtp_compute_efv(mtp_handle* h, const mtp_nlist* nl, const double* x_dev, con
 
 /* Same evaluation as mtp_compute_efv with precision MTP_MIXED and no
  * parameter gradient, but the call allocates no device memory: its
- * fixed-point position scratch is a 2 MiB array built into the library, so
+ * scratch (fixed-point positions and an FP32 force accumulator) is a
+ * 2.75 MiB array built into the library, so
  * n_atoms may be at most 65536 (larger n fails with MTP_ERR_ARG; use
  * mtp_compute_efv then).  For callers that must not have a library allocate
  * during a step: an MD engine that sets its whole device-memory budget at

@@ -404,6 +404,40 @@ class Level:
 # ---------------------------------------------------------------------------
 
 
+def tree_sum(terms):
+    """Balanced sum expression (short dependency chains)."""
+    terms = list(terms)
+    if not terms:
+        return "R(0)"
+    while len(terms) > 1:
+        nxt = []
+        for k in range(0, len(terms) - 1, 2):
+            nxt.append("(%s + %s)" % (terms[k], terms[k + 1]))
+        if len(terms) % 2:
+            nxt.append(terms[-1])
+        terms = nxt
+    return terms[0]
+
+
+def emit_dot(lines, ind, name, pairs, declare=True, max_chain=6):
+    """name = sum_k x_k * y_k as interleaved FMA chains of length <= max_chain,
+    combined by a balanced sum."""
+    nacc = max(1, min(4, (len(pairs) + max_chain - 1) // max_chain))
+    accs = []
+    for a in range(nacc):
+        sub = pairs[a::nacc]
+        if not sub:
+            continue
+        acc = name if nacc == 1 else "%s_p%d" % (name, a)
+        x0, y0 = sub[0]
+        lines.append(ind + "%s%s = %s * %s;" % ("R " if (declare or nacc > 1) else "", acc, x0, y0))
+        for x, y in sub[1:]:
+            lines.append(ind + "%s = fmadd(%s, %s, %s);" % (acc, x, y, acc))
+        accs.append(acc)
+    if nacc > 1:
+        lines.append(ind + "%s%s = %s;" % ("R " if declare else "", name, tree_sum(accs)))
+
+
 def _mono_name(K):
     return "u%d%d%d" % K
 
@@ -440,15 +474,39 @@ def _closure(keys):
     return need
 
 
+def _monomial_source(K):
+    """The lower monomial and coordinate that u^K is formed from."""
+    if K[0] > 0:
+        return (K[0] - 1, K[1], K[2]), "ux"
+    if K[1] > 0:
+        return (K[0], K[1] - 1, K[2]), "uy"
+    return (K[0], K[1], K[2] - 1), "uz"
+
+
+def _monomial_order(maxnu):
+    return [K for nu in range(0, maxnu + 1) for K in multi_indices(nu)]
+
+
 def emit_moments(lv: Level):
-    """M[c] += f[mu] * u^K for every component (mu, K)."""
+    """M[c] += f[mu] * u^K for every component (mu, K).  Each monomial is
+    formed and consumed at once, so few monomials are live at a time."""
     L = []
     ind = "    "
     L.append("  template <class R>")
     L.append("  __device__ __forceinline__ static void moments(R* __restrict__ M, const R* __restrict__ f, R ux, R uy, R uz) {")
-    _emit_monomials(L, max(lv.nu_max), ind)
+    L.append(ind + "const R u000 = R(1);")
+    by_k = defaultdict(list)
     for c, (mu, K) in enumerate(lv.comps):
-        L.append(ind + "M[%d] = fmadd(f[%d], %s, M[%d]);" % (c, mu, _mono_name(K), c))
+        by_k[K].append((c, mu))
+    for K in _monomial_order(max(lv.nu_max)):
+        if sum(K) > 0:
+            src, co = _monomial_source(K)
+            L.append(ind + "const R %s = %s * %s;" % (_mono_name(K), _mono_name(src), co))
+        for c, mu in by_k.get(K, []):
+            if sum(K) == 0:
+                L.append(ind + "M[%d] += f[%d];" % (c, mu))
+            else:
+                L.append(ind + "M[%d] = fmadd(f[%d], %s, M[%d]);" % (c, mu, _mono_name(K), c))
     L.append("  }")
     return L
 
@@ -461,56 +519,61 @@ def emit_pair_adjoint(lv: Level):
         g = u * sum_mu (df_mu S_mu - f_mu T_mu / r) + (1/r) sum_mu f_mu G_mu
 
     (grad of u^K along the sphere is (grad_u u^K - |K| u^K u) / r).  S_mu is
-    also returned: it is the chain-rule factor of d E / d c[mu, k, zi, zj]."""
+    also returned: it is the chain-rule factor of d E / d c[mu, k, zi, zj].
+    The code visits monomials u^J in generation order and adds every term that
+    uses u^J right away: D[mu,J] u^J into S_{mu,|J|}, and D[mu,K] u^J into
+    G_{mu,d,K_d} for K = J + e_d (grad u^K has component K_d u^{K - e_d})."""
     L = []
     ind = "    "
     L.append("  template <class R>")
     L.append("  __device__ __forceinline__ static void pair_adjoint(const R* __restrict__ D, const R* __restrict__ f, "
              "const R* __restrict__ df, R ux, R uy, R uz, R rinv, R& gx, R& gy, R& gz, R* __restrict__ S) {")
-    _emit_monomials(L, max(lv.nu_max), ind)
+    L.append(ind + "const R u000 = R(1);")
+    comp = lv.comp_index
+    declared = set()
+
+    def acc(name, x, y):
+        if name in declared:
+            L.append(ind + "%s = fmadd(%s, %s, %s);" % (name, x, y, name))
+        else:
+            declared.add(name)
+            L.append(ind + "R %s = %s * %s;" % (name, x, y))
+
+    maxnu = max(lv.nu_max)
+    for J in _monomial_order(maxnu):
+        if sum(J) > 0:
+            src, co = _monomial_source(J)
+            L.append(ind + "const R %s = %s * %s;" % (_mono_name(J), _mono_name(src), co))
+        mj = _mono_name(J)
+        for mu in range(lv.nmu):
+            c = comp.get((mu, J))
+            if c is not None:
+                acc("s%d_%d" % (mu, sum(J)), "D[%d]" % c, mj)
+            for d, dn in enumerate("xyz"):
+                K = list(J)
+                K[d] += 1
+                c2 = comp.get((mu, tuple(K)))
+                if c2 is not None:
+                    acc("g%d%s%d" % (mu, dn, K[d]), "D[%d]" % c2, mj)
     L.append(ind + "R ax = R(0), ay = R(0), az = R(0), radial = R(0);")
     for mu in range(lv.nmu):
-        comps = [(c, K) for c, (m, K) in enumerate(lv.comps) if m == mu]
-        if not comps:
+        nus = sorted({sum(K) for (m, K) in lv.comps if m == mu})
+        if not nus:
             L.append(ind + "S[%d] = R(0);" % mu)
             continue
-        bynu = defaultdict(list)
-        for c, K in comps:
-            bynu[sum(K)].append((c, K))
-        # S_{mu,nu}
-        for nu, lst in sorted(bynu.items()):
-            c0, K0 = lst[0]
-            expr = "D[%d] * %s" % (c0, _mono_name(K0))
-            L.append(ind + "R s%d_%d = %s;" % (mu, nu, expr))
-            for c, K in lst[1:]:
-                L.append(ind + "s%d_%d = fmadd(D[%d], %s, s%d_%d);" % (mu, nu, c, _mono_name(K), mu, nu))
-        nus = sorted(bynu)
-        L.append(ind + "const R S%d = %s;" % (mu, " + ".join("s%d_%d" % (mu, n) for n in nus)))
+        L.append(ind + "const R S%d = %s;" % (mu, tree_sum("s%d_%d" % (mu, n) for n in nus)))
         tnus = [n for n in nus if n > 0]
-        if tnus:
-            L.append(ind + "const R T%d = %s;" % (mu, " + ".join(("s%d_%d" % (mu, n)) if n == 1 else
-                                                                ("R(%d) * s%d_%d" % (n, mu, n)) for n in tnus)))
-        else:
-            L.append(ind + "const R T%d = R(0);" % mu)
+        L.append(ind + "const R T%d = %s;" % (mu, tree_sum(("s%d_%d" % (mu, n)) if n == 1 else
+                                                            ("R(%d) * s%d_%d" % (n, mu, n)) for n in tnus)))
         L.append(ind + "S[%d] = S%d;" % (mu, mu))
-        # G_mu grouped by the integer factor K_d
-        for d, dn in enumerate("xyz"):
-            groups = defaultdict(list)
-            for c, K in comps:
-                if K[d] > 0:
-                    low = list(K)
-                    low[d] -= 1
-                    groups[K[d]].append((c, tuple(low)))
+        for dn in "xyz":
             parts = []
-            for a, lst in sorted(groups.items()):
+            for a in range(1, maxnu + 1):
                 name = "g%d%s%d" % (mu, dn, a)
-                c0, k0 = lst[0]
-                L.append(ind + "R %s = D[%d] * %s;" % (name, c0, _mono_name(k0)))
-                for c, k in lst[1:]:
-                    L.append(ind + "%s = fmadd(D[%d], %s, %s);" % (name, c, _mono_name(k), name))
-                parts.append(name if a == 1 else "R(%d) * %s" % (a, name))
+                if name in declared:
+                    parts.append(name if a == 1 else "R(%d) * %s" % (a, name))
             if parts:
-                L.append(ind + "a%s = fmadd(f[%d], %s, a%s);" % (dn, mu, " + ".join(parts), dn))
+                L.append(ind + "a%s = fmadd(f[%d], %s, a%s);" % (dn, mu, tree_sum(parts), dn))
         L.append(ind + "radial = fmadd(df[%d], S%d, radial);" % (mu, mu))
         L.append(ind + "radial = fmadd(-f[%d] * rinv, T%d, radial);" % (mu, mu))
     L.append(ind + "gx = fmadd(ux, radial, ax * rinv);")
@@ -559,17 +622,14 @@ def emit_contract(lv: Level):
         wname[n] = wn
         for ki, K in enumerate(multi_indices(rank)):
             terms = [(comp_ref(a, (K[0] + P[0], K[1] + P[1], K[2] + P[2])), wn[j]) for j, P in enumerate(Ps)]
-            expr = "%s * %s" % terms[0]
-            L.append(ind + "R v%d_%d = %s;" % (n, ki, expr))
-            for x, y in terms[1:]:
-                L.append(ind + "v%d_%d = fmadd(%s, %s, v%d_%d);" % (n, ki, x, y, n, ki))
+            emit_dot(L, ind, "v%d_%d" % (n, ki), terms)
     # graph values
     for gi, roots in enumerate(lv.roots):
         parts = []
         for w, node in roots:
             ref = comp_ref(node, (0, 0, 0))
             parts.append(ref if w == 1 else "R(%d) * %s" % (w, ref))
-        L.append(ind + "const R G%d = %s;" % (gi, " + ".join(parts)))
+        L.append(ind + "const R G%d = %s;" % (gi, tree_sum(parts)))
     # basis values, energy
     L.append(ind + "R E = R(0);")
     for a, b in enumerate(lv.bases):
@@ -587,7 +647,7 @@ def emit_contract(lv: Level):
         for a, others in gbar[gi]:
             prod = " * ".join("G%d" % k for k in others)
             terms.append("R(xi[%d])" % a + (" * " + prod if prod else ""))
-        L.append(ind + "const R Gb%d = %s;" % (gi, " + ".join(terms) if terms else "R(0)"))
+        L.append(ind + "const R Gb%d = %s;" % (gi, tree_sum(terms)))
     # node adjoints
     adj = defaultdict(list)          # (node, comp index) -> list of expressions
     for gi, roots in enumerate(lv.roots):
@@ -605,7 +665,7 @@ def emit_contract(lv: Level):
                 names.append(None)
                 continue
             nm = "b%d_%d" % (n, ki)
-            L.append(ind + "const R %s = %s;" % (nm, " + ".join(ex)))
+            L.append(ind + "const R %s = %s;" % (nm, tree_sum(ex)))
             names.append(nm)
         return names
 
@@ -642,14 +702,12 @@ def emit_contract(lv: Level):
             P = Ps[j]
             w = multinomial_weight(P)
             nm = "c%d_%d" % (n, j)
-            L.append(ind + "R %s = %s * %s;" % (nm, lst[0][0], lst[0][1]))
-            for x, y in lst[1:]:
-                L.append(ind + "%s = fmadd(%s, %s, %s);" % (nm, x, y, nm))
+            emit_dot(L, ind, nm, lst)
             bidx = j
             adj[(b, bidx)].append(nm if w == 1 else "R(%d) * %s" % (w, nm))
     for c in range(len(lv.comps)):
         ex = dcontrib.get(c)
-        L.append(ind + "D[%d] = %s;" % (c, " + ".join(ex) if ex else "R(0)"))
+        L.append(ind + "D[%d] = %s;" % (c, tree_sum(ex)))
     L.append(ind + "return E;")
     L.append("  }")
     return L

@@ -31,17 +31,30 @@ __device__ __forceinline__ void flag_status(int* status, int code) {
   if (status) atomicCAS(status, 0, code);
 }
 
-// Pair vector r_ij = x_j + n.H - x_i.
+// Pair vector r_ij = x_j + n.H - x_i, in two steps so that the loads of the
+// next pair can be issued before the current pair is processed:
+// fetch(j) loads what the pair needs from atom j, vec() forms the vector.
 template <class R> struct PairGeom;
 
 template <> struct PairGeom<double> {
   // FP64: positions directly, shift s = (n1 a + n2 b) + n3 c.
+  struct Load {
+    double x, y, z;
+    int species;
+  };
   double xi, yi, zi;
   __device__ __forceinline__ void load_centre(const EfvArgs& a, int64_t i) {
     xi = a.x[3 * i]; yi = a.x[3 * i + 1]; zi = a.x[3 * i + 2];
   }
-  __device__ __forceinline__ int species_of(const EfvArgs& a, int32_t j) const { return __ldg(a.z + j); }
-  __device__ __forceinline__ void vec(const EfvArgs& a, int32_t j, int32_t img, double& dx, double& dy,
+  __device__ __forceinline__ Load fetch(const EfvArgs& a, int32_t j) const {
+    Load l;
+    l.x = __ldg(a.x + 3 * (int64_t)j);
+    l.y = __ldg(a.x + 3 * (int64_t)j + 1);
+    l.z = __ldg(a.x + 3 * (int64_t)j + 2);
+    l.species = __ldg(a.z + j);
+    return l;
+  }
+  __device__ __forceinline__ void vec(const EfvArgs& a, const Load& l, int32_t img, double& dx, double& dy,
                                       double& dz) const {
     int n1, n2, n3;
     unpack_image(img, n1, n2, n3);
@@ -49,40 +62,104 @@ template <> struct PairGeom<double> {
     const double sx = ((double)n1 * c[0] + (double)n2 * c[3]) + (double)n3 * c[6];
     const double sy = ((double)n1 * c[1] + (double)n2 * c[4]) + (double)n3 * c[7];
     const double sz = ((double)n1 * c[2] + (double)n2 * c[5]) + (double)n3 * c[8];
-    dx = (__ldg(a.x + 3 * j) + sx) - xi;
-    dy = (__ldg(a.x + 3 * j + 1) + sy) - yi;
-    dz = (__ldg(a.x + 3 * j + 2) + sz) - zi;
+    dx = (l.x + sx) - xi;
+    dy = (l.y + sy) - yi;
+    dz = (l.z + sz) - zi;
   }
 };
+
+// Exact int -> float for |v| < 2^22 without a conversion instruction: the
+// integer is added to the mantissa of 1.5 * 2^23.
+__device__ __forceinline__ float small_int_to_float(int v) {
+  return __int_as_float(0x4B400000 + v) - 12582912.0f;
+}
+
+// 32.32 fixed-point difference (int64) to a float in units of one cell:
+// v = hi 2^16 + lo with hi = floor(v / 2^16) and 0 <= lo < 2^16.  Both parts
+// are exact as floats (hi through the mantissa trick while |hi| < 2^22, that
+// is up to 64 cells), so the single rounding is in the final sum, and no
+// conversion runs on the FP64 pipe.
+__device__ __forceinline__ float fixed_to_float(long long v) {
+  const int hi = (int)(v >> 16);
+  const float lo = small_int_to_float((int)(v & 0xFFFF));
+  const float h = ((unsigned)(hi + (1 << 22)) < (1u << 23)) ? small_int_to_float(hi) : (float)hi;
+  return fmaf(h, 65536.0f, lo) * 2.3283064365386963e-10f;
+}
 
 template <> struct PairGeom<float> {
   // Mixed: exact integer difference of 32.32 fixed-point fractional
   // coordinates plus the image, converted to FP32 and mapped by the cell.
+  struct Load {
+    longlong2 xy, zs;   // (qx, qy), (qz, species)
+    int species;
+  };
   long long qx, qy, qz;
   __device__ __forceinline__ void load_centre(const EfvArgs& a, int64_t i) {
     const longlong2 p = *reinterpret_cast<const longlong2*>(a.xq + 4 * i);
-    qx = p.x; qy = p.y;
-    qz = a.xq[4 * i + 2];
+    const longlong2 q = *reinterpret_cast<const longlong2*>(a.xq + 4 * i + 2);
+    qx = p.x; qy = p.y; qz = q.x;
   }
-  __device__ __forceinline__ int species_of(const EfvArgs& a, int32_t j) const {
-    return (int)__ldg(a.xq + 4 * (int64_t)j + 3);
+  __device__ __forceinline__ Load fetch(const EfvArgs& a, int32_t j) const {
+    Load l;
+    l.xy = __ldg(reinterpret_cast<const longlong2*>(a.xq + 4 * (int64_t)j));
+    l.zs = __ldg(reinterpret_cast<const longlong2*>(a.xq + 4 * (int64_t)j + 2));
+    l.species = (int)l.zs.y;
+    return l;
   }
-  __device__ __forceinline__ void vec(const EfvArgs& a, int32_t j, int32_t img, float& dx, float& dy,
+  __device__ __forceinline__ void vec(const EfvArgs& a, const Load& l, int32_t img, float& dx, float& dy,
                                       float& dz) const {
     int n1, n2, n3;
     unpack_image(img, n1, n2, n3);
-    const longlong2 p = __ldg(reinterpret_cast<const longlong2*>(a.xq + 4 * (int64_t)j));
-    const long long pz = __ldg(a.xq + 4 * (int64_t)j + 2);
-    const float s = 2.3283064365386963e-10f;  // 2^-32
-    const float fx = __ll2float_rn(p.x - qx + ((long long)n1 << 32)) * s;
-    const float fy = __ll2float_rn(p.y - qy + ((long long)n2 << 32)) * s;
-    const float fz = __ll2float_rn(pz - qz + ((long long)n3 << 32)) * s;
+    const float fx = fixed_to_float(l.xy.x - qx + ((long long)n1 << 32));
+    const float fy = fixed_to_float(l.xy.y - qy + ((long long)n2 << 32));
+    const float fz = fixed_to_float(l.zs.x - qz + ((long long)n3 << 32));
     const float* c = a.cellf;
     dx = fmaf(fz, c[6], fmaf(fy, c[3], fx * c[0]));
     dy = fmaf(fz, c[7], fmaf(fy, c[4], fx * c[1]));
     dz = fmaf(fz, c[8], fmaf(fy, c[5], fx * c[2]));
   }
 };
+
+// Neighbour stream with software prefetch: the entry two pairs ahead and
+// the atom data one pair ahead are in flight while a pair is processed.
+template <class R>
+struct PairStream {
+  using Geom = PairGeom<R>;
+  int64_t k, end;
+  int32_t j1, im1, j2, im2;
+  typename Geom::Load l1;
+  __device__ __forceinline__ void start(const EfvArgs& a, const Geom& g, int64_t beg, int64_t end_) {
+    k = beg;
+    end = end_;
+    j1 = im1 = j2 = im2 = 0;
+    if (k < end) { j1 = __ldg(a.nbr_j + k); im1 = __ldg(a.nbr_img + k); }
+    if (k + 1 < end) { j2 = __ldg(a.nbr_j + k + 1); im2 = __ldg(a.nbr_img + k + 1); }
+    if (k < end) l1 = g.fetch(a, j1);
+  }
+  __device__ __forceinline__ bool next(const EfvArgs& a, const Geom& g, int32_t& j, int32_t& img,
+                                       typename Geom::Load& l) {
+    if (k >= end) return false;
+    j = j1; img = im1; l = l1;
+    j1 = j2; im1 = im2;
+    if (k + 1 < end) l1 = g.fetch(a, j1);
+    if (k + 2 < end) { j2 = __ldg(a.nbr_j + k + 2); im2 = __ldg(a.nbr_img + k + 2); }
+    ++k;
+    return true;
+  }
+};
+
+// Force accumulation: FP64 atomics on the FP64 path; FP32 atomics into the
+// FP32 accumulator on the mixed path (converted to FP64 once per atom at the end).
+__device__ __forceinline__ void scatter_force(const EfvArgs& a, int64_t k, double gx, double gy, double gz) {
+  atomicAdd(a.forces + 3 * k, gx);
+  atomicAdd(a.forces + 3 * k + 1, gy);
+  atomicAdd(a.forces + 3 * k + 2, gz);
+}
+__device__ __forceinline__ void scatter_force(const EfvArgs& a, int64_t k, float gx, float gy, float gz) {
+  atomicAdd(a.forces_f + 3 * k, gx);
+  atomicAdd(a.forces_f + 3 * k + 1, gy);
+  atomicAdd(a.forces_f + 3 * k + 2, gz);
+}
 
 __device__ __forceinline__ float rsqrt_r(float v) { return rsqrtf(v); }
 __device__ __forceinline__ double rsqrt_r(double v) { return rsqrt(v); }
@@ -203,12 +280,14 @@ __global__ void __launch_bounds__(kEfvThreads) efv_kernel(const EfvArgs a) {
     R M[LV::NCOMP];
 #pragma unroll
     for (int c = 0; c < LV::NCOMP; ++c) M[c] = R(0);
-    for (int64_t k = beg; k < end; ++k) {
-      const int32_t j = __ldg(a.nbr_j + k);
-      const int32_t img = __ldg(a.nbr_img + k);
-      const int zj = geom.species_of(a, j);
+    PairStream<R> ps;
+    int32_t j, img;
+    typename PairGeom<R>::Load lj;
+    ps.start(a, geom, beg, end);
+    while (ps.next(a, geom, j, img, lj)) {
+      const int zj = lj.species;
       R dx, dy, dz;
-      geom.vec(a, j, img, dx, dy, dz);
+      geom.vec(a, lj, img, dx, dy, dz);
       const R r2 = fmadd(dz, dz, fmadd(dy, dy, dx * dx));
       const R rinv = rsqrt_r(r2);
       const R r = r2 * rinv;
@@ -222,12 +301,11 @@ __global__ void __launch_bounds__(kEfvThreads) efv_kernel(const EfvArgs a) {
     a.e_atom[i] = e_i;
 
     R fx = R(0), fy = R(0), fz = R(0);
-    for (int64_t k = beg; k < end; ++k) {
-      const int32_t j = __ldg(a.nbr_j + k);
-      const int32_t img = __ldg(a.nbr_img + k);
-      const int zj = geom.species_of(a, j);
+    ps.start(a, geom, beg, end);
+    while (ps.next(a, geom, j, img, lj)) {
+      const int zj = lj.species;
       R dx, dy, dz;
-      geom.vec(a, j, img, dx, dy, dz);
+      geom.vec(a, lj, img, dx, dy, dz);
       const R r2 = fmadd(dz, dz, fmadd(dy, dy, dx * dx));
       const R rinv = rsqrt_r(r2);
       const R r = r2 * rinv;
@@ -237,9 +315,7 @@ __global__ void __launch_bounds__(kEfvThreads) efv_kernel(const EfvArgs a) {
       R gx, gy, gz, Smu[NMU];
       LV::template pair_adjoint<R>(D, f, df, dx * rinv, dy * rinv, dz * rinv, rinv, gx, gy, gz, Smu);
       fx += gx; fy += gy; fz += gz;
-      atomicAdd(a.forces + 3 * (int64_t)j, -(double)gx);
-      atomicAdd(a.forces + 3 * (int64_t)j + 1, -(double)gy);
-      atomicAdd(a.forces + 3 * (int64_t)j + 2, -(double)gz);
+      scatter_force(a, j, -gx, -gy, -gz);
       w[0] = fmadd(-gx, dx, w[0]);
       w[1] = fmadd(-gy, dy, w[1]);
       w[2] = fmadd(-gz, dz, w[2]);
@@ -256,9 +332,7 @@ __global__ void __launch_bounds__(kEfvThreads) efv_kernel(const EfvArgs a) {
         }
       }
     }
-    atomicAdd(a.forces + 3 * i, (double)fx);
-    atomicAdd(a.forces + 3 * i + 1, (double)fy);
-    atomicAdd(a.forces + 3 * i + 2, (double)fz);
+    scatter_force(a, i, fx, fy, fz);
     if (!isfinite(e_i) || !isfinite((double)fx) || !isfinite((double)fy) || !isfinite((double)fz))
       flag_status(a.status, MTP_ERR_NONFINITE);
     if (DTHETA) atomicAdd(s_cnt + zi, 1);

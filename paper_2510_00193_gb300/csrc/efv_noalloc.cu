@@ -10,19 +10,20 @@
 // This entry point uses a fixed scratch array compiled into the library
 // instead; the caller still provides every input and output array.
 //
-// The scratch.  g_noalloc_positions below is a file-scope __device__ array
-// sized for kNoAllocMaxAtoms atoms (32 bytes each, 2 MiB in all).  Every GPU
-// that loads this library holds it until the process exits.  Host code cannot
-// use the array's name as a device address (in host code it names a host-side
+// The scratch.  g_noalloc_scratch below is a file-scope __device__ array
+// sized for kNoAllocMaxAtoms atoms: 32 bytes of fixed-point position and 12
+// bytes of FP32 force accumulator per atom (2.75 MiB in all).  Every GPU that
+// loads this library holds it until the process exits.  Host code cannot use
+// the array's name as a device address (in host code it names a host-side
 // stand-in), so the first call on each device looks the address up with
 // cudaGetSymbolAddress, with that device current, and caches it.  Make that
 // first call on a device before any stream capture starts.
 //
 // Sharing.  All calls on a device share the one array and it keeps whatever
-// the previous call wrote.  Nothing in it has to start at zero: each call
-// overwrites the entries of all its atoms before reading them.  Calls that
-// overlap on the GPU (different streams or host threads at once) race on the
-// array; issue them one after another.
+// the previous call wrote.  Each call overwrites the positions of all its
+// atoms before reading them and clears the force accumulator of its atoms
+// before adding to it.  Calls that overlap on the GPU (different streams or
+// host threads at once) race on the array; issue them one after another.
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -36,11 +37,13 @@ namespace mtp {
 constexpr int64_t kNoAllocMaxAtoms = 65536;
 constexpr int kNoAllocMaxDevices = 64;
 
-static __device__ __align__(256) long long g_noalloc_positions[4 * kNoAllocMaxAtoms];
+// [4 * kNoAllocMaxAtoms] int64 positions, then [3 * kNoAllocMaxAtoms] floats
+static __device__ __align__(256) long long g_noalloc_scratch[4 * kNoAllocMaxAtoms + 3 * kNoAllocMaxAtoms / 2];
 
 __global__ void fixed_point_kernel(const double* __restrict__ x, const int32_t* __restrict__ z, int64_t n,
                                    double h0, double h1, double h2, double h3, double h4, double h5, double h6,
                                    double h7, double h8, int S, long long* __restrict__ out, int* __restrict__ status);
+__global__ void forces_to_fp64_kernel(const float* __restrict__ f, int64_t n3, double* __restrict__ out);
 
 static std::mutex g_noalloc_mutex;
 static long long* g_noalloc_address[kNoAllocMaxDevices] = {nullptr};
@@ -57,7 +60,7 @@ static int noalloc_scratch(long long** out) {
   std::lock_guard<std::mutex> lock(g_noalloc_mutex);
   if (!g_noalloc_address[dev]) {
     void* p = nullptr;
-    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_positions);
+    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
     if (e != cudaSuccess || !p) {
       set_error("mtp_compute_efv_noalloc: cudaGetSymbolAddress of the scratch array failed: %s",
                 cudaGetErrorString(e));
@@ -106,7 +109,8 @@ extern "C" int mtp_compute_efv_noalloc(mtp_handle* h, const mtp_nlist* nl, const
   if (rc != MTP_OK) return rc;
 
   cudaStream_t s = (cudaStream_t)stream;
-  MTP_TRY_CUDA(cudaMemsetAsync(forces, 0, sizeof(double) * 3 * (size_t)n, s));
+  float* forces_f = reinterpret_cast<float*>(scratch + 4 * kNoAllocMaxAtoms);
+  if (n == 0) MTP_TRY_CUDA(cudaMemsetAsync(forces, 0, sizeof(double) * 3 * (size_t)n, s));
   MTP_TRY_CUDA(cudaMemsetAsync(virial, 0, sizeof(double) * 6, s));
   MTP_TRY_CUDA(cudaMemsetAsync(e_total, 0, sizeof(double), s));
   if (n == 0) return MTP_OK;
@@ -125,6 +129,7 @@ extern "C" int mtp_compute_efv_noalloc(mtp_handle* h, const mtp_nlist* nl, const
                                                                  hi[6], hi[7], hi[8], h->n_species, scratch,
                                                                  h->status.as<int>());
   MTP_TRY_CUDA(cudaGetLastError());
+  MTP_TRY_CUDA(cudaMemsetAsync(forces_f, 0, sizeof(float) * 3 * (size_t)n, s));
 
   EfvArgs a;
   std::memset(&a, 0, sizeof(a));
@@ -152,6 +157,7 @@ extern "C" int mtp_compute_efv_noalloc(mtp_handle* h, const mtp_nlist* nl, const
   a.xi_f = h->xi_f.as<float>();
   a.e_atom = e_atom;
   a.forces = forces;
+  a.forces_f = forces_f;
   a.virial = virial;
   a.e_total = e_total;
   a.dtheta = nullptr;
@@ -163,5 +169,7 @@ extern "C" int mtp_compute_efv_noalloc(mtp_handle* h, const mtp_nlist* nl, const
     rc = h->ops->efv(a, MTP_MIXED, false, s);
     if (rc != MTP_OK) return rc;
   }
+  forces_to_fp64_kernel<<<(unsigned)((3 * n + 255) / 256), 256, 0, s>>>(forces_f, 3 * n, forces);
+  MTP_TRY_CUDA(cudaGetLastError());
   return MTP_OK;
 }

@@ -75,6 +75,12 @@ __global__ void fixed_point_kernel(const double* __restrict__ x, const int32_t* 
   out[4 * i + 3] = (long long)zi;
 }
 
+// Mixed path: the FP32 force accumulator converted to the FP64 output.
+__global__ void forces_to_fp64_kernel(const float* __restrict__ f, int64_t n3, double* __restrict__ out) {
+  const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (k < n3) out[k] = (double)f[k];
+}
+
 __global__ void species_check_kernel(const int32_t* __restrict__ z, int64_t n, int S, int* __restrict__ status) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n && (z[i] < 0 || z[i] >= S)) atomicCAS(status, 0, MTP_ERR_ARG);
@@ -223,6 +229,7 @@ void mtp_free(mtp_handle* h) {
   h->xi_f.release();
   h->status.release();
   h->xq.release();
+  h->forces_f.release();
   delete h;
 }
 
@@ -345,7 +352,7 @@ int mtp_compute_efv(mtp_handle* h, const mtp_nlist* nl, const double* x, const i
     return MTP_ERR_ARG;
   }
   cudaStream_t s = (cudaStream_t)stream;
-  MTP_TRY_CUDA(cudaMemsetAsync(forces, 0, sizeof(double) * 3 * (size_t)n, s));
+  if (precision == MTP_FP64 || n == 0) MTP_TRY_CUDA(cudaMemsetAsync(forces, 0, sizeof(double) * 3 * (size_t)n, s));
   MTP_TRY_CUDA(cudaMemsetAsync(virial, 0, sizeof(double) * 6, s));
   MTP_TRY_CUDA(cudaMemsetAsync(e_total, 0, sizeof(double), s));
   if (dtheta) MTP_TRY_CUDA(cudaMemsetAsync(dtheta, 0, sizeof(double) * h->n_params, s));
@@ -404,6 +411,9 @@ int mtp_compute_efv(mtp_handle* h, const mtp_nlist* nl, const double* x, const i
                                               h->n_species, h->xq.as<long long>(), a.status);
     MTP_TRY_CUDA(cudaGetLastError());
     a.xq = h->xq.as<long long>();
+    if ((rc = h->forces_f.ensure(sizeof(float) * 3 * (size_t)n)) != MTP_OK) return rc;
+    a.forces_f = h->forces_f.as<float>();
+    MTP_TRY_CUDA(cudaMemsetAsync(a.forces_f, 0, sizeof(float) * 3 * (size_t)n, s));
   } else {
     species_check_kernel<<<blocks, 256, 0, s>>>(z, n, h->n_species, a.status);
     MTP_TRY_CUDA(cudaGetLastError());
@@ -414,6 +424,10 @@ int mtp_compute_efv(mtp_handle* h, const mtp_nlist* nl, const double* x, const i
     a.atom_end = b + chunk < n ? b + chunk : n;
     int rc = h->ops->efv(a, precision, dtheta != nullptr, s);
     if (rc != MTP_OK) return rc;
+  }
+  if (precision == MTP_MIXED) {
+    forces_to_fp64_kernel<<<(unsigned)((3 * n + 255) / 256), 256, 0, s>>>(a.forces_f, 3 * n, forces);
+    MTP_TRY_CUDA(cudaGetLastError());
   }
   return MTP_OK;
 }

@@ -64,6 +64,7 @@ struct EfvArgs {
   const float* xi_f;
   double* e_atom;
   double* forces;
+  float* forces_f;          // mixed path: FP32 force accumulator [N][3], converted at the end
   double* virial;
   double* e_total;
   double* dtheta;           // nullable
@@ -91,6 +92,7 @@ struct mtp_handle {
   std::vector<double> h_species, h_radial, h_xi;
   mtp::DevBuf species, radial_d, xi_d, radial_f, xi_f, status;
   mtp::DevBuf xq;        // fixed-point positions scratch
+  mtp::DevBuf forces_f;  // FP32 force accumulator (mixed path)
 };
 
 struct mtp_nlist {
