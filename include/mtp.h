@@ -131,6 +131,57 @@ int mtp_compute_efv(mtp_handle* h, const mtp_nlist* nl, const double* x_dev, con
                     double* e_atom_dev, double* forces_dev, double* virial_dev, double* e_total_dev,
                     double* dEdtheta_dev, void* stream);
 
+/* Extrapolation grade (paper Sec. 2.1: configuration and neighbourhood mode
+ * with a selection and a break threshold; Sec. 2.3: select above tau_sel,
+ * halt above tau_brk).  With b_i the basis row of atom i (the m basis
+ * functions B_alpha of its neighbourhood):
+ *   neighbourhood mode: gamma_i = max_k |(b_i A^-1)_k|, flags_i bit 0 =
+ *     gamma_i > tau_sel, bit 1 = gamma_i > tau_brk;
+ *   configuration mode: gamma_cfg = max_k |((sum_i b_i) A_cfg^-1)_k|.
+ * a_inv_dev / a_inv_cfg_dev: DEVICE, m x m row-major FP64 inverses of the
+ * active sets (either may be NULL, not both).  Basis rows and products are
+ * FP64 throughout; chunk_atoms bounds the FP64 row scratch (0 = 262144).
+ * Outputs: gamma_dev [N] FP64 and flags_dev [N] uint8 (DEVICE, neighbourhood
+ * mode); gamma_max, gamma_cfg, n_ambiguous on the HOST (nullable):
+ * n_ambiguous counts grades within their FP64 error bound of a threshold.
+ * Synchronises `stream`.  Returns MTP_STATUS_BREAK when the largest grade
+ * exceeds tau_brk, MTP_OK otherwise, or an error code. */
+int mtp_compute_grade(mtp_handle* h, const mtp_nlist* nl, const double* x_dev, const int32_t* z_dev,
+                      int64_t n_atoms, const double* cell, const double* a_inv_dev, const double* a_inv_cfg_dev,
+                      double tau_sel, double tau_brk, int64_t chunk_atoms, double* gamma_dev, uint8_t* flags_dev,
+                      double* gamma_max, double* gamma_cfg, int64_t* n_ambiguous, void* stream);
+
+/* Batches of many small periodic configurations (SURVEY workload: thousands
+ * of 8..256-atom cells), evaluated in one persistent launch.
+ * mtp_batch_create: atom_off (HOST, n_cfg + 1, atom_off[0] = 0) splits the
+ * concatenated atoms into configurations; cells (HOST, n_cfg x 9, rows a, b,
+ * c per configuration); pbc (HOST, 3, for all); x_dev the positions used to
+ * build the per-configuration neighbour lists (same definition and order as
+ * mtp_build_neighbors, indices global).  atoms_per_block: 32..256 (multiple
+ * of 32) or 0 for 64; mtp_batch_tune can pick it by timing.  Synchronises. */
+typedef struct mtp_batch mtp_batch;
+int mtp_batch_create(mtp_handle* h, int32_t n_cfg, const int64_t* atom_off, const double* cells,
+                     const int32_t* pbc, const double* x_dev, int32_t atoms_per_block, mtp_batch** out,
+                     void* stream);
+/* The batch's combined neighbour list (owned by the batch). */
+int mtp_batch_nlist(const mtp_batch* b, const mtp_nlist** nl);
+/* Energies, forces, virials and (optionally) dE/dtheta of every
+ * configuration.  Work items (configuration, up to atoms_per_block atoms) are
+ * taken from a device counter by a grid of (SM count x resident blocks)
+ * blocks.  Outputs (DEVICE, overwritten): e_cfg [n_cfg], e_atom [N] (or
+ * NULL), forces [N][3], virial [n_cfg][6], dEdtheta [n_cfg][n_params] (or
+ * NULL).  Asynchronous; allocates nothing. */
+int mtp_compute_batch(mtp_handle* h, const mtp_batch* b, const double* x_dev, const int32_t* z_dev,
+                      int32_t precision, double* e_cfg_dev, double* e_atom_dev, double* forces_dev,
+                      double* virial_dev, double* dEdtheta_dev, void* stream);
+/* Times mtp_compute_batch with 32, 64, 128 and 256 atoms per block (CUDA
+ * events, after warm-up) and keeps the fastest (*chosen).  The outputs are
+ * scratch for the trial runs.  Synchronises. */
+int mtp_batch_tune(mtp_handle* h, mtp_batch* b, const double* x_dev, const int32_t* z_dev, int32_t precision,
+                   int32_t want_dtheta, int32_t* chosen, double* e_cfg_dev, double* forces_dev,
+                   double* virial_dev, double* dEdtheta_dev, void* stream);
+void mtp_batch_free(mtp_batch* b);
+
 /* Same evaluation as mtp_compute_efv with precision MTP_MIXED and no
  * parameter gradient, but the call allocates no device memory: its
  * scratch (fixed-point positions and an FP32 force accumulator) is a

@@ -5,6 +5,7 @@ data, the way a fitted MLIP potential file is data.  Run from the repo root:
 
     python -m oracle.make_potentials            # all workloads
     python -m oracle.make_potentials bcc-l8-s1  # one
+    python -m oracle.make_potentials active     # grade active sets (after the potentials)
 
 Normalisation (a reading: the paper's workloads use trained potentials, which
 are not available).  Raw coefficients are drawn by ``synth.raw_potential``:
@@ -112,5 +113,68 @@ def main(argv):
         print(name, "m =", pot["m"])
 
 
+
+
+# ---------------------------------------------------------------------------
+# Active sets for the extrapolation grade (paper Sec. 2.1: configuration and
+# neighbourhood mode; MaxVol of Goreinov et al. 2010 as cited in Sec. 1)
+# ---------------------------------------------------------------------------
+
+ACTIVE = {
+    # neighbourhood mode: pool = every atom of a 20^3-cell BCC box (16,000 atoms, sigma 0.05 A)
+    # configuration mode: pool = summed basis rows of 4m 128-atom BCC boxes (sigma 0.05 A,
+    # every cell vector scaled by an independent factor in [0.98, 1.02])
+    "bcc-l16-s1": dict(pool_cells=(20, 20, 20), a=3.16, sigma=0.05, stream=5),
+}
+
+
+def make_active_set(name: str) -> dict:
+    import json as _json
+    spec = ACTIVE[name]
+    with open(os.path.join(OUT, name + ".json")) as fh:
+        pot = _json.load(fh)
+    model = O.load_model(pot)
+    st = synth.crystal("bcc", spec["pool_cells"], spec["a"], spec["sigma"], pot["n_species"], spec["stream"], sub=8)
+    nl = O.neighbor_list(st.x, st.cell, st.pbc, pot["r_cut"])
+    pool = O.basis_matrix(model, st.x, st.z, st.cell, nl)
+    rows, a_inv, iters = O.maxvol(pool, delta=0.01)
+    m = pool.shape[1]
+    g = synth.rng(spec["stream"], 60)
+    cfg_rows = []
+    for k in range(4 * m):
+        c = synth.crystal("bcc", (4, 4, 4), spec["a"], spec["sigma"], pot["n_species"], spec["stream"], sub=100 + k)
+        scale = g.uniform(0.98, 1.02, size=3)
+        cell = c.cell * scale[:, None]
+        x = c.x @ np.linalg.inv(c.cell) @ cell
+        nlc = O.neighbor_list(x, cell, c.pbc, pot["r_cut"])
+        cfg_rows.append(O.basis_matrix(model, x, c.z, cell, nlc).sum(axis=0))
+    cfg_pool = np.array(cfg_rows)
+    cfg_sel, a_inv_cfg, iters_cfg = O.maxvol(cfg_pool, delta=0.01)
+    return {
+        "potential": name,
+        "m": m,
+        "a_inv": [float(v) for v in a_inv.ravel()],
+        "active_rows": [int(r) for r in rows],
+        "cond": float(np.linalg.cond(pool[rows])),
+        "maxvol_iterations": int(iters),
+        "a_inv_cfg": [float(v) for v in a_inv_cfg.ravel()],
+        "active_cfg": [int(r) for r in cfg_sel],
+        "cond_cfg": float(np.linalg.cond(cfg_pool[cfg_sel])),
+        "maxvol_iterations_cfg": int(iters_cfg),
+        "note": "A^-1 of the MaxVol active sets (delta 0.01), FP64 Gauss-Jordan; row-major m x m",
+    }
+
+
+def main_active(argv):
+    for name in argv[1:] or list(ACTIVE):
+        d = make_active_set(name)
+        with open(os.path.join(OUT, name + "-active.json"), "w") as fh:
+            json.dump(d, fh, indent=0)
+        print(name, "cond", d["cond"], "cond_cfg", d["cond_cfg"], "iters", d["maxvol_iterations"], d["maxvol_iterations_cfg"])
+
+
 if __name__ == "__main__":
-    main(sys.argv)
+    if len(sys.argv) > 1 and sys.argv[1] == "active":
+        main_active(sys.argv[1:])
+    else:
+        main(sys.argv)

@@ -18,7 +18,8 @@ from ._lib import MTP_FP64, MTP_MIXED, MtpError, check
 
 __all__ = [
     "MTP_FP64", "MTP_MIXED", "MtpError", "Potential", "NeighborList", "mtp_basis_info", "mtp_basis_table",
-    "mtp_load_params", "mtp_build_neighbors", "mtp_compute_efv", "mtp_compute_efv_noalloc", "mtp_device_status",
+    "mtp_load_params", "mtp_build_neighbors", "mtp_compute_efv", "mtp_compute_efv_noalloc", "mtp_compute_grade",
+    "mtp_device_status", "Batch", "mtp_batch_create", "mtp_compute_batch", "mtp_batch_tune",
     "library_path",
 ]
 
@@ -246,6 +247,128 @@ def mtp_compute_efv_noalloc(potential: Potential, nlist: NeighborList, x, z, cel
         _dptr(out["virial"], torch.float64, 6, "virial"), _dptr(out["e_total"], torch.float64, 1, "e_total"),
         _stream_ptr(stream)))
     return out
+
+
+def mtp_compute_grade(potential: Potential, nlist: NeighborList, x, z, cell, a_inv=None, a_inv_cfg=None,
+                      tau_sel=2.0, tau_brk=10.0, chunk_atoms=0, out=None, stream=None) -> dict:
+    """Extrapolation grades.  a_inv / a_inv_cfg: [m, m] float64 CUDA tensors
+    (inverse active sets for neighbourhood / configuration mode).  Returns
+    gamma [N] float64 and flags [N] uint8 (CUDA tensors, neighbourhood mode),
+    gamma_max, gamma_cfg, n_ambiguous and status (1 = above the break
+    threshold)."""
+    import torch
+    n = x.shape[0]
+    m = potential.m
+    dev = x.device
+    if out is None:
+        out = {"gamma": torch.empty(n, dtype=torch.float64, device=dev) if a_inv is not None else None,
+               "flags": torch.empty(n, dtype=torch.uint8, device=dev) if a_inv is not None else None}
+    c = _host_d(cell, 9)
+    gmax, gcfg = ctypes.c_double(), ctypes.c_double()
+    amb = ctypes.c_int64()
+    rc = check(_lib.load().mtp_compute_grade(
+        potential.handle, nlist.handle, _dptr(x, torch.float64, 3 * n, "x"), _dptr(z, torch.int32, n, "z"), n,
+        c.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+        _dptr(a_inv, torch.float64, m * m, "a_inv") if a_inv is not None else None,
+        _dptr(a_inv_cfg, torch.float64, m * m, "a_inv_cfg") if a_inv_cfg is not None else None,
+        float(tau_sel), float(tau_brk), int(chunk_atoms),
+        _dptr(out["gamma"], torch.float64, n, "gamma") if a_inv is not None else None,
+        _dptr(out["flags"], torch.uint8, n, "flags") if a_inv is not None else None,
+        ctypes.byref(gmax), ctypes.byref(gcfg), ctypes.byref(amb), _stream_ptr(stream)))
+    out.update(gamma_max=gmax.value, gamma_cfg=gcfg.value, n_ambiguous=amb.value, status=rc)
+    return out
+
+
+class Batch:
+    """Owns an mtp_batch: many small configurations with their neighbour lists."""
+
+    def __init__(self, potential: Potential, atom_off, cells, x, pbc=(1, 1, 1), atoms_per_block=0, stream=None):
+        import torch
+        lib = _lib.load()
+        off = np.ascontiguousarray(np.asarray(atom_off, dtype=np.int64))
+        cl = np.ascontiguousarray(np.asarray(cells, dtype=np.float64).reshape(-1))
+        p = np.ascontiguousarray(np.asarray(pbc, dtype=np.int32).reshape(3))
+        self.n_cfg = len(off) - 1
+        self.n_atoms = int(off[-1])
+        if cl.size != 9 * self.n_cfg:
+            raise ValueError("cells must hold 9 values per configuration")
+        self._b = ctypes.c_void_p()
+        self._pot = potential
+        check(lib.mtp_batch_create(potential.handle, self.n_cfg, off.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)),
+                                   cl.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                   p.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
+                                   _dptr(x, torch.float64, 3 * self.n_atoms, "x"), int(atoms_per_block),
+                                   ctypes.byref(self._b), _stream_ptr(stream)))
+
+    @property
+    def handle(self):
+        return self._b
+
+    def nlist_tensors(self, stream=None):
+        """(offsets, j, images) of the combined neighbour list."""
+        nl = ctypes.c_void_p()
+        check(_lib.load().mtp_batch_nlist(self._b, ctypes.byref(nl)))
+        view = NeighborList()
+        view._nl = nl
+        try:
+            return view.to_tensors(stream)
+        finally:
+            view._nl = ctypes.c_void_p()
+
+    def __del__(self):
+        b = getattr(self, "_b", None)
+        if b is not None and b.value:
+            try:
+                _lib.load().mtp_batch_free(b)
+            except Exception:
+                pass
+            self._b = None
+
+
+def _batch_out(potential, batch, x, dtheta):
+    import torch
+    dev = x.device
+    return {"e_cfg": torch.empty(batch.n_cfg, dtype=torch.float64, device=dev),
+            "e_atom": torch.empty(batch.n_atoms, dtype=torch.float64, device=dev),
+            "forces": torch.empty((batch.n_atoms, 3), dtype=torch.float64, device=dev),
+            "virial": torch.empty((batch.n_cfg, 6), dtype=torch.float64, device=dev),
+            "dtheta": torch.empty((batch.n_cfg, potential.n_params), dtype=torch.float64, device=dev)
+            if dtheta else None}
+
+
+def mtp_batch_create(potential, atom_off, cells, x, pbc=(1, 1, 1), atoms_per_block=0, stream=None) -> Batch:
+    return Batch(potential, atom_off, cells, x, pbc, atoms_per_block, stream)
+
+
+def mtp_compute_batch(potential: Potential, batch: Batch, x, z, precision=MTP_MIXED, dtheta=False, out=None,
+                      stream=None) -> dict:
+    """Per-configuration energies e_cfg, per-atom e_atom, forces, per-configuration
+    virials and (optionally) dE/dtheta [n_cfg, n_params], as CUDA tensors."""
+    import torch
+    n = batch.n_atoms
+    if out is None:
+        out = _batch_out(potential, batch, x, dtheta)
+    check(_lib.load().mtp_compute_batch(
+        potential.handle, batch.handle, _dptr(x, torch.float64, 3 * n, "x"), _dptr(z, torch.int32, n, "z"),
+        int(precision), _dptr(out["e_cfg"], torch.float64, batch.n_cfg, "e_cfg"),
+        _dptr(out["e_atom"], torch.float64, n, "e_atom"), _dptr(out["forces"], torch.float64, 3 * n, "forces"),
+        _dptr(out["virial"], torch.float64, 6 * batch.n_cfg, "virial"),
+        _dptr(out["dtheta"], torch.float64, batch.n_cfg * potential.n_params, "dtheta") if dtheta else None,
+        _stream_ptr(stream)))
+    return out
+
+
+def mtp_batch_tune(potential: Potential, batch: Batch, x, z, precision=MTP_MIXED, dtheta=False, stream=None) -> int:
+    """Picks the atoms-per-block of the batched launch by timing; returns it."""
+    import torch
+    out = _batch_out(potential, batch, x, dtheta)
+    chosen = ctypes.c_int32()
+    n = batch.n_atoms
+    check(_lib.load().mtp_batch_tune(
+        potential.handle, batch.handle, _dptr(x, torch.float64, 3 * n, "x"), _dptr(z, torch.int32, n, "z"),
+        int(precision), int(bool(dtheta)), ctypes.byref(chosen), _dptr(out["e_cfg"]), _dptr(out["forces"]),
+        _dptr(out["virial"]), _dptr(out["dtheta"]) if dtheta else None, _stream_ptr(stream)))
+    return chosen.value
 
 
 def mtp_device_status(potential: Potential, stream=None) -> int:

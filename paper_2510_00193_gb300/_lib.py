@@ -59,6 +59,13 @@ SIGNATURES = {
     "mtp_nlist_copy": (ctypes.c_int, [_VP, _VP, _VP, _VP, _VP]),
     "mtp_free_nlist": (None, [_VP]),
     "mtp_compute_efv": (ctypes.c_int, [_VP, _VP, _VP, _VP, _I64, _P_D, _I32, _I64, _VP, _VP, _VP, _VP, _VP, _VP]),
+    "mtp_compute_grade": (ctypes.c_int, [_VP, _VP, _VP, _VP, _I64, _P_D, _VP, _VP, ctypes.c_double, ctypes.c_double,
+                                         _I64, _VP, _VP, _P_D, _P_D, _P_I64, _VP]),
+    "mtp_batch_create": (ctypes.c_int, [_VP, _I32, _P_I64, _P_D, _P_I32, _VP, _I32, ctypes.POINTER(_VP), _VP]),
+    "mtp_batch_nlist": (ctypes.c_int, [_VP, ctypes.POINTER(_VP)]),
+    "mtp_compute_batch": (ctypes.c_int, [_VP, _VP, _VP, _VP, _I32, _VP, _VP, _VP, _VP, _VP, _VP]),
+    "mtp_batch_tune": (ctypes.c_int, [_VP, _VP, _VP, _VP, _I32, _I32, _P_I32, _VP, _VP, _VP, _VP, _VP]),
+    "mtp_batch_free": (None, [_VP]),
     "mtp_compute_efv_noalloc": (ctypes.c_int, [_VP, _VP, _VP, _VP, _I64, _P_D, _I64, _VP, _VP, _VP, _VP, _VP]),
     "mtp_device_status": (ctypes.c_int, [_VP, _VP]),
     "mtp_last_error": (ctypes.c_char_p, []),

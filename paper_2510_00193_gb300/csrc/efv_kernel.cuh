@@ -43,8 +43,10 @@ template <> struct PairGeom<double> {
     int species;
   };
   double xi, yi, zi;
-  __device__ __forceinline__ void load_centre(const EfvArgs& a, int64_t i) {
+  const double* c;   // cell rows of the configuration
+  __device__ __forceinline__ void load_centre(const EfvArgs& a, int64_t i, const double* cell) {
     xi = a.x[3 * i]; yi = a.x[3 * i + 1]; zi = a.x[3 * i + 2];
+    c = cell;
   }
   __device__ __forceinline__ Load fetch(const EfvArgs& a, int32_t j) const {
     Load l;
@@ -58,7 +60,6 @@ template <> struct PairGeom<double> {
                                       double& dz) const {
     int n1, n2, n3;
     unpack_image(img, n1, n2, n3);
-    const double* c = a.cell;
     const double sx = ((double)n1 * c[0] + (double)n2 * c[3]) + (double)n3 * c[6];
     const double sy = ((double)n1 * c[1] + (double)n2 * c[4]) + (double)n3 * c[7];
     const double sz = ((double)n1 * c[2] + (double)n2 * c[5]) + (double)n3 * c[8];
@@ -94,10 +95,12 @@ template <> struct PairGeom<float> {
     int species;
   };
   long long qx, qy, qz;
-  __device__ __forceinline__ void load_centre(const EfvArgs& a, int64_t i) {
+  const float* c;    // cell rows of the configuration
+  __device__ __forceinline__ void load_centre(const EfvArgs& a, int64_t i, const float* cell) {
     const longlong2 p = *reinterpret_cast<const longlong2*>(a.xq + 4 * i);
     const longlong2 q = *reinterpret_cast<const longlong2*>(a.xq + 4 * i + 2);
     qx = p.x; qy = p.y; qz = q.x;
+    c = cell;
   }
   __device__ __forceinline__ Load fetch(const EfvArgs& a, int32_t j) const {
     Load l;
@@ -113,7 +116,6 @@ template <> struct PairGeom<float> {
     const float fx = fixed_to_float(l.xy.x - qx + ((long long)n1 << 32));
     const float fy = fixed_to_float(l.xy.y - qy + ((long long)n2 << 32));
     const float fz = fixed_to_float(l.zs.x - qz + ((long long)n3 << 32));
-    const float* c = a.cellf;
     dx = fmaf(fz, c[6], fmaf(fy, c[3], fx * c[0]));
     dy = fmaf(fz, c[7], fmaf(fy, c[4], fx * c[1]));
     dz = fmaf(fz, c[8], fmaf(fy, c[5], fx * c[2]));
@@ -160,6 +162,10 @@ __device__ __forceinline__ void scatter_force(const EfvArgs& a, int64_t k, float
   atomicAdd(a.forces_f + 3 * k + 1, gy);
   atomicAdd(a.forces_f + 3 * k + 2, gz);
 }
+
+template <class R> __device__ __forceinline__ const R* cell_of(const EfvArgs& a);
+template <> __device__ __forceinline__ const double* cell_of<double>(const EfvArgs& a) { return a.cell; }
+template <> __device__ __forceinline__ const float* cell_of<float>(const EfvArgs& a) { return a.cellf; }
 
 __device__ __forceinline__ float rsqrt_r(float v) { return rsqrtf(v); }
 __device__ __forceinline__ double rsqrt_r(double v) { return rsqrt(v); }
@@ -220,165 +226,202 @@ __host__ __device__ __forceinline__ size_t efv_red_offset(int SS, int nq, int m)
   return (bytes + 15) & ~size_t(15);
 }
 
-template <class LV, class R, bool DTHETA>
-__global__ void __launch_bounds__(kEfvThreads) efv_kernel(const EfvArgs a) {
-  constexpr int NMU = LV::NMU;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int S = a.n_species;
-  const int SS = S * S;
-  const int nq = a.n_q;
-  const int cstride = (NMU * nq) | 1;  // odd stride: species-pair blocks fall on distinct banks
-  R* s_c = reinterpret_cast<R*>(smem_raw);
-  R* s_xi = s_c + SS * cstride;
-  R* s_dc = s_xi + a.m;                 // DTHETA: [SS][NMU][nq]
-  R* s_dxi = s_dc + (DTHETA ? SS * NMU * nq : 0);
-  // FP64 reduction scratch after the R-typed arrays, on a 16-byte boundary
-  const size_t red_off = efv_red_offset<R, NMU, DTHETA>(SS, nq, a.m);
-  double* s_red = reinterpret_cast<double*>(smem_raw + red_off);  // 8 doubles per warp
-  int* s_cnt = reinterpret_cast<int*>(s_red + 8 * (kEfvThreads / 32));
+constexpr int kMaxWarps = 8;   // blocks of up to 256 threads
 
-  const R* radial_src = nullptr;
-  const R* xi_src = nullptr;
-  if constexpr (sizeof(R) == 8) {
-    radial_src = reinterpret_cast<const R*>(a.radial_d);
-    xi_src = reinterpret_cast<const R*>(a.xi_d);
-  } else {
-    radial_src = reinterpret_cast<const R*>(a.radial_f);
-    xi_src = reinterpret_cast<const R*>(a.xi_f);
-  }
-  for (int t = threadIdx.x; t < NMU * nq * SS; t += blockDim.x) {
-    // global layout [mu][k][zi][zj] -> shared [zi*S+zj][mu][k]
-    const int p = t % SS;
-    const int mk = t / SS;
-    s_c[p * cstride + mk] = radial_src[t];
-  }
-  for (int t = threadIdx.x; t < a.m; t += blockDim.x) s_xi[t] = xi_src[t];
-  if (DTHETA) {
-    for (int t = threadIdx.x; t < SS * NMU * nq; t += blockDim.x) s_dc[t] = R(0);
-    for (int t = threadIdx.x; t < a.m; t += blockDim.x) s_dxi[t] = R(0);
-    for (int t = threadIdx.x; t < S; t += blockDim.x) s_cnt[t] = 0;
-  }
-  __syncthreads();
+template <class R, int NMU, bool DTHETA>
+__host__ __device__ __forceinline__ size_t efv_smem_bytes(int SS, int nq, int m) {
+  return efv_red_offset<R, NMU, DTHETA>(SS, nq, m) + sizeof(double) * 8 * kMaxWarps + sizeof(int) * kMaxSpecies;
+}
 
-  const R rcut = R(a.r_cut);
-  const R mid = R(0.5 * (a.r_min + a.r_cut));
-  const R scale = R(2.0 / (a.r_cut - a.r_min));
-  const int64_t i = a.atom_begin + (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  const bool active = i < a.atom_end;
+// Shared-memory view: radial coefficients [zi*S+zj][mu][k] (odd stride: the
+// species-pair blocks fall on distinct banks), xi, and with DTHETA the
+// per-block gradient accumulators.
+template <class R, int NMU, bool DTHETA>
+struct EfvShared {
+  R* c;
+  R* xi;
+  R* dc;      // [SS][NMU][nq]
+  R* dxi;     // [m]
+  double* red;
+  int* cnt;   // [S]
+  int S, SS, nq, cstride, m;
+  R rcut, mid, scale;
 
-  double e_i = 0.0;
-  R w[6] = {R(0), R(0), R(0), R(0), R(0), R(0)};
-  R Bv[DTHETA ? LV::NBASIS : 1];
-#pragma unroll
-  for (int t = 0; t < (DTHETA ? LV::NBASIS : 1); ++t) Bv[t] = R(0);
-
-  if (active) {
-    PairGeom<R> geom;
-    geom.load_centre(a, i);
-    const int zi = __ldg(a.z + i);
-    const int64_t beg = __ldg(a.offsets + i), end = __ldg(a.offsets + i + 1);
-    R M[LV::NCOMP];
-#pragma unroll
-    for (int c = 0; c < LV::NCOMP; ++c) M[c] = R(0);
-    PairStream<R> ps;
-    int32_t j, img;
-    typename PairGeom<R>::Load lj;
-    ps.start(a, geom, beg, end);
-    while (ps.next(a, geom, j, img, lj)) {
-      const int zj = lj.species;
-      R dx, dy, dz;
-      geom.vec(a, lj, img, dx, dy, dz);
-      const R r2 = fmadd(dz, dz, fmadd(dy, dy, dx * dx));
-      const R rinv = rsqrt_r(r2);
-      const R r = r2 * rinv;
-      R f[NMU];
-      radial<R, NMU, false, false>(s_c + (zi * S + zj) * cstride, nq, r, mid, scale, rcut, f, nullptr, nullptr);
-      LV::template moments<R>(M, f, dx * rinv, dy * rinv, dz * rinv);
+  __device__ __forceinline__ void setup(const EfvArgs& a, unsigned char* raw) {
+    S = a.n_species;
+    SS = S * S;
+    nq = a.n_q;
+    m = a.m;
+    cstride = (NMU * nq) | 1;
+    c = reinterpret_cast<R*>(raw);
+    xi = c + SS * cstride;
+    dc = xi + m;
+    dxi = dc + (DTHETA ? SS * NMU * nq : 0);
+    red = reinterpret_cast<double*>(raw + efv_red_offset<R, NMU, DTHETA>(SS, nq, m));
+    cnt = reinterpret_cast<int*>(red + 8 * kMaxWarps);
+    const R* radial_src;
+    const R* xi_src;
+    if constexpr (sizeof(R) == 8) {
+      radial_src = reinterpret_cast<const R*>(a.radial_d);
+      xi_src = reinterpret_cast<const R*>(a.xi_d);
+    } else {
+      radial_src = reinterpret_cast<const R*>(a.radial_f);
+      xi_src = reinterpret_cast<const R*>(a.xi_f);
     }
-    R D[LV::NCOMP];
-    const R ei = LV::template contract<R, DTHETA>(M, s_xi, D, Bv);
-    e_i = a.species_energy[zi] + (double)ei;
-    a.e_atom[i] = e_i;
+    for (int t = threadIdx.x; t < NMU * nq * SS; t += blockDim.x) {
+      // global layout [mu][k][zi][zj] -> shared [zi*S+zj][mu][k]
+      c[(t % SS) * cstride + t / SS] = radial_src[t];
+    }
+    for (int t = threadIdx.x; t < m; t += blockDim.x) xi[t] = xi_src[t];
+    rcut = R(a.r_cut);
+    mid = R(0.5 * (a.r_min + a.r_cut));
+    scale = R(2.0 / (a.r_cut - a.r_min));
+  }
 
-    R fx = R(0), fy = R(0), fz = R(0);
-    ps.start(a, geom, beg, end);
-    while (ps.next(a, geom, j, img, lj)) {
-      const int zj = lj.species;
-      R dx, dy, dz;
-      geom.vec(a, lj, img, dx, dy, dz);
-      const R r2 = fmadd(dz, dz, fmadd(dy, dy, dx * dx));
-      const R rinv = rsqrt_r(r2);
-      const R r = r2 * rinv;
-      R f[NMU], df[NMU], q[DTHETA ? kMaxQ : 1];
-      const R* cblk = s_c + (zi * S + zj) * cstride;
-      radial<R, NMU, true, DTHETA>(cblk, nq, r, mid, scale, rcut, f, df, q);
-      R gx, gy, gz, Smu[NMU];
-      LV::template pair_adjoint<R>(D, f, df, dx * rinv, dy * rinv, dz * rinv, rinv, gx, gy, gz, Smu);
-      fx += gx; fy += gy; fz += gz;
-      scatter_force(a, j, -gx, -gy, -gz);
-      w[0] = fmadd(-gx, dx, w[0]);
-      w[1] = fmadd(-gy, dy, w[1]);
-      w[2] = fmadd(-gz, dz, w[2]);
-      w[3] = fmadd(R(-0.5), fmadd(gx, dy, gy * dx), w[3]);
-      w[4] = fmadd(R(-0.5), fmadd(gx, dz, gz * dx), w[4]);
-      w[5] = fmadd(R(-0.5), fmadd(gy, dz, gz * dy), w[5]);
-      if (DTHETA) {
-        R* dst = s_dc + (zi * S + zj) * NMU * nq;
+  __device__ __forceinline__ void zero_gradients() {
+    if (!DTHETA) return;
+    for (int t = threadIdx.x; t < SS * NMU * nq; t += blockDim.x) dc[t] = R(0);
+    for (int t = threadIdx.x; t < m; t += blockDim.x) dxi[t] = R(0);
+    for (int t = threadIdx.x; t < S; t += blockDim.x) cnt[t] = 0;
+  }
+};
+
+// Everything one centre atom contributes: its site energy (also stored in
+// e_atom), its force terms (scattered), its virial terms (w) and, with
+// DTHETA, its basis values (Bv) and radial-coefficient gradient (shared
+// accumulators).  `cell` holds the rows of its configuration's cell.
+template <class LV, class R, bool DTHETA>
+__device__ __forceinline__ void efv_atom(const EfvArgs& a, const EfvShared<R, LV::NMU, DTHETA>& sm, int64_t i,
+                                         const R* cell, double& e_i, R* w, R* Bv) {
+  constexpr int NMU = LV::NMU;
+  PairGeom<R> geom;
+  geom.load_centre(a, i, cell);
+  const int zi = __ldg(a.z + i);
+  const int64_t beg = __ldg(a.offsets + i), end = __ldg(a.offsets + i + 1);
+  R M[LV::NCOMP];
 #pragma unroll
-        for (int mu = 0; mu < NMU; ++mu) {
+  for (int c = 0; c < LV::NCOMP; ++c) M[c] = R(0);
+  PairStream<R> ps;
+  int32_t j, img;
+  typename PairGeom<R>::Load lj;
+  ps.start(a, geom, beg, end);
+  while (ps.next(a, geom, j, img, lj)) {
+    R dx, dy, dz;
+    geom.vec(a, lj, img, dx, dy, dz);
+    const R r2 = fmadd(dz, dz, fmadd(dy, dy, dx * dx));
+    const R rinv = rsqrt_r(r2);
+    const R r = r2 * rinv;
+    R f[NMU];
+    radial<R, NMU, false, false>(sm.c + (zi * sm.S + lj.species) * sm.cstride, sm.nq, r, sm.mid, sm.scale, sm.rcut, f,
+                                 nullptr, nullptr);
+    LV::template moments<R>(M, f, dx * rinv, dy * rinv, dz * rinv);
+  }
+  R D[LV::NCOMP];
+  const R ei = LV::template contract<R, DTHETA>(M, sm.xi, D, Bv);
+  e_i = a.species_energy[zi] + (double)ei;
+  a.e_atom[i] = e_i;
+
+  R fx = R(0), fy = R(0), fz = R(0);
+  ps.start(a, geom, beg, end);
+  while (ps.next(a, geom, j, img, lj)) {
+    const int zj = lj.species;
+    R dx, dy, dz;
+    geom.vec(a, lj, img, dx, dy, dz);
+    const R r2 = fmadd(dz, dz, fmadd(dy, dy, dx * dx));
+    const R rinv = rsqrt_r(r2);
+    const R r = r2 * rinv;
+    R f[NMU], df[NMU], q[DTHETA ? kMaxQ : 1];
+    radial<R, NMU, true, DTHETA>(sm.c + (zi * sm.S + zj) * sm.cstride, sm.nq, r, sm.mid, sm.scale, sm.rcut, f, df, q);
+    R gx, gy, gz, Smu[NMU];
+    LV::template pair_adjoint<R>(D, f, df, dx * rinv, dy * rinv, dz * rinv, rinv, gx, gy, gz, Smu);
+    fx += gx; fy += gy; fz += gz;
+    scatter_force(a, j, -gx, -gy, -gz);
+    w[0] = fmadd(-gx, dx, w[0]);
+    w[1] = fmadd(-gy, dy, w[1]);
+    w[2] = fmadd(-gz, dz, w[2]);
+    w[3] = fmadd(R(-0.5), fmadd(gx, dy, gy * dx), w[3]);
+    w[4] = fmadd(R(-0.5), fmadd(gx, dz, gz * dx), w[4]);
+    w[5] = fmadd(R(-0.5), fmadd(gy, dz, gz * dy), w[5]);
+    if (DTHETA) {
+      R* dst = sm.dc + (zi * sm.S + zj) * NMU * sm.nq;
 #pragma unroll
-          for (int kk = 0; kk < kMaxQ; ++kk)
-            if (kk < nq) atomicAdd(dst + mu * nq + kk, q[kk] * Smu[mu]);
-        }
+      for (int mu = 0; mu < NMU; ++mu) {
+#pragma unroll
+        for (int kk = 0; kk < kMaxQ; ++kk)
+          if (kk < sm.nq) atomicAdd(dst + mu * sm.nq + kk, q[kk] * Smu[mu]);
       }
     }
-    scatter_force(a, i, fx, fy, fz);
-    if (!isfinite(e_i) || !isfinite((double)fx) || !isfinite((double)fy) || !isfinite((double)fz))
-      flag_status(a.status, MTP_ERR_NONFINITE);
-    if (DTHETA) atomicAdd(s_cnt + zi, 1);
   }
+  scatter_force(a, i, fx, fy, fz);
+  if (!isfinite(e_i) || !isfinite((double)fx) || !isfinite((double)fy) || !isfinite((double)fz))
+    flag_status(a.status, MTP_ERR_NONFINITE);
+  if (DTHETA) atomicAdd(sm.cnt + zi, 1);
+}
 
-  // FP64 block reductions: energy and virial.
+// Block-wide FP64 reduction of the block's energy, virial and gradient into
+// e_out[0], w_out[0..6) and theta_out (layout [ s | c[mu][k][zi][zj] | xi ]).
+// Must be reached by every thread of the block.
+template <class LV, class R, bool DTHETA>
+__device__ __forceinline__ void efv_block_flush(const EfvShared<R, LV::NMU, DTHETA>& sm, double e_i, const R* w,
+                                                const R* Bv, double* e_out, double* w_out, double* theta_out) {
+  constexpr int NMU = LV::NMU;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int nwarps = (blockDim.x + 31) >> 5;
   double vals[7] = {e_i, (double)w[0], (double)w[1], (double)w[2], (double)w[3], (double)w[4], (double)w[5]};
 #pragma unroll
   for (int t = 0; t < 7; ++t) vals[t] = warp_sum(vals[t]);
   if (lane == 0) {
 #pragma unroll
-    for (int t = 0; t < 7; ++t) s_red[warp * 8 + t] = vals[t];
+    for (int t = 0; t < 7; ++t) sm.red[warp * 8 + t] = vals[t];
   }
   if (DTHETA) {
 #pragma unroll
     for (int t = 0; t < (DTHETA ? LV::NBASIS : 1); ++t) {
       const double v = warp_sum((double)Bv[t]);
-      if (lane == 0) atomicAdd(s_dxi + t, R(v));
+      if (lane == 0) atomicAdd(sm.dxi + t, R(v));
     }
   }
   __syncthreads();
   if (threadIdx.x < 7) {
     double acc = 0.0;
-    for (int wi = 0; wi < kEfvThreads / 32; ++wi) acc += s_red[wi * 8 + threadIdx.x];
-    if (threadIdx.x == 0) atomicAdd(a.e_total, acc);
-    else atomicAdd(a.virial + threadIdx.x - 1, acc);
+    for (int wi = 0; wi < nwarps; ++wi) acc += sm.red[wi * 8 + threadIdx.x];
+    if (threadIdx.x == 0) atomicAdd(e_out, acc);
+    else atomicAdd(w_out + threadIdx.x - 1, acc);
   }
   if (DTHETA) {
-    // theta = [ s (S) | c [mu][k][zi][zj] | xi (m) ]
-    for (int t = threadIdx.x; t < S; t += blockDim.x) atomicAdd(a.dtheta + t, (double)s_cnt[t]);
+    const int S = sm.S, SS = sm.SS, nq = sm.nq;
+    for (int t = threadIdx.x; t < S; t += blockDim.x) atomicAdd(theta_out + t, (double)sm.cnt[t]);
     for (int t = threadIdx.x; t < SS * NMU * nq; t += blockDim.x) {
       const int p = t / (NMU * nq);
       const int mk = t % (NMU * nq);
-      atomicAdd(a.dtheta + S + (int64_t)mk * SS + p, (double)s_dc[t]);
+      atomicAdd(theta_out + S + (int64_t)mk * SS + p, (double)sm.dc[t]);
     }
-    for (int t = threadIdx.x; t < a.m; t += blockDim.x)
-      atomicAdd(a.dtheta + S + (int64_t)NMU * nq * SS + t, (double)s_dxi[t]);
+    for (int t = threadIdx.x; t < sm.m; t += blockDim.x)
+      atomicAdd(theta_out + S + (int64_t)NMU * nq * SS + t, (double)sm.dxi[t]);
   }
+}
+
+template <class LV, class R, bool DTHETA>
+__global__ void __launch_bounds__(kEfvThreads) efv_kernel(const EfvArgs a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  EfvShared<R, LV::NMU, DTHETA> sm;
+  sm.setup(a, smem_raw);
+  sm.zero_gradients();
+  __syncthreads();
+  const int64_t i = a.atom_begin + (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  double e_i = 0.0;
+  R w[6] = {R(0), R(0), R(0), R(0), R(0), R(0)};
+  R Bv[DTHETA ? LV::NBASIS : 1];
+#pragma unroll
+  for (int t = 0; t < (DTHETA ? LV::NBASIS : 1); ++t) Bv[t] = R(0);
+  if (i < a.atom_end) efv_atom<LV, R, DTHETA>(a, sm, i, cell_of<R>(a), e_i, w, Bv);
+  efv_block_flush<LV, R, DTHETA>(sm, e_i, w, Bv, a.e_total, a.virial, a.dtheta);
 }
 
 template <class LV, class R, bool DTHETA>
 int efv_launch_typed(const EfvArgs& a, cudaStream_t stream) {
   const int SS = a.n_species * a.n_species;
-  size_t bytes = efv_red_offset<R, LV::NMU, DTHETA>(SS, a.n_q, a.m);
-  bytes += sizeof(double) * 8 * (kEfvThreads / 32) + sizeof(int) * kMaxSpecies;
+  const size_t bytes = efv_smem_bytes<R, LV::NMU, DTHETA>(SS, a.n_q, a.m);
   auto kern = efv_kernel<LV, R, DTHETA>;
   if (bytes > 48 * 1024) {
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);

@@ -1,0 +1,250 @@
+// Extrapolation grade: gamma_i = max_k |(b_i A^-1)_k| (neighbourhood mode) and
+// gamma_cfg = max_k |((sum_i b_i) A_cfg^-1)_k| (configuration mode), with the
+// selection and break thresholds of paper Sec. 2.1 / Sec. 2.3.
+//
+// Precision.  Everything is FP64.  On active sets drawn from near-perfect
+// lattices the product b_i A^-1 cancels by a factor sum_j |b_ij A_jk| / gamma_i
+// of about 5e7 (median over a sigma = 0.15 A BCC box against a sigma = 0.05 A
+// pool), so neither FP32 basis values nor a TF32/BF16 product can decide a
+// flag; FP64 leaves a relative error of about 1e-8.  Each row carries the bound
+// eps_i = kGradeRelErr * sum_j |b_ij| max_k |A_jk|; a row whose grade lies
+// within eps_i of a threshold is counted as ambiguous (its flag is still the
+// FP64 comparison).
+//
+// gemm_grade_kernel: 64 rows x all m columns per block of 256 threads, K in
+// blocks of 16 staged in shared memory, 4 x 8 FP64 accumulators per thread,
+// fused row maximum, bound, flags and the running maximum grade.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstring>
+
+#include "mtp_internal.cuh"
+
+namespace mtp {
+
+constexpr double kGradeRelErr = 1e-12;
+constexpr int kGemmBM = 64, kGemmBK = 16, kGemmBN = 128;
+
+__global__ void __launch_bounds__(256) gemm_grade_kernel(const double* __restrict__ rows, int64_t n, int m,
+                                                         const double* __restrict__ ainv,
+                                                         const double* __restrict__ amax, double tau_sel,
+                                                         double tau_brk, double* __restrict__ gamma,
+                                                         uint8_t* __restrict__ flags,
+                                                         unsigned long long* __restrict__ gmax_bits,
+                                                         unsigned long long* __restrict__ n_ambiguous) {
+  __shared__ double As[kGemmBK][kGemmBM + 1];
+  __shared__ double Bs[kGemmBK][kGemmBN];
+  __shared__ double red[kGemmBM][17];
+  const int tid = threadIdx.x;
+  const int ty = tid / 16, tx = tid % 16;
+  const int64_t row0 = (int64_t)blockIdx.x * kGemmBM;
+  double acc[4][8];
+#pragma unroll
+  for (int r = 0; r < 4; ++r)
+#pragma unroll
+    for (int c = 0; c < 8; ++c) acc[r][c] = 0.0;
+  for (int kb = 0; kb < m; kb += kGemmBK) {
+#pragma unroll
+    for (int t = 0; t < (kGemmBM * kGemmBK) / 256; ++t) {
+      const int e = tid + 256 * t;
+      const int rr = e / kGemmBK, kk = e % kGemmBK;
+      const int64_t gr = row0 + rr;
+      As[kk][rr] = (gr < n && kb + kk < m) ? rows[gr * m + kb + kk] : 0.0;
+    }
+#pragma unroll
+    for (int t = 0; t < (kGemmBK * kGemmBN) / 256; ++t) {
+      const int e = tid + 256 * t;
+      const int kk = e / kGemmBN, cc = e % kGemmBN;
+      Bs[kk][cc] = (kb + kk < m && cc < m) ? ainv[(int64_t)(kb + kk) * m + cc] : 0.0;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < kGemmBK; ++kk) {
+      double av[4], bv[8];
+#pragma unroll
+      for (int r = 0; r < 4; ++r) av[r] = As[kk][ty * 4 + r];
+#pragma unroll
+      for (int c = 0; c < 8; ++c) bv[c] = Bs[kk][tx + 16 * c];
+#pragma unroll
+      for (int r = 0; r < 4; ++r)
+#pragma unroll
+        for (int c = 0; c < 8; ++c) acc[r][c] = fma(av[r], bv[c], acc[r][c]);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int r = 0; r < 4; ++r) {
+    double mx = 0.0;
+#pragma unroll
+    for (int c = 0; c < 8; ++c) mx = fmax(mx, fabs(acc[r][c]));
+    red[ty * 4 + r][tx] = mx;
+  }
+  __syncthreads();
+  if (tid < kGemmBM) {
+    const int64_t gr = row0 + tid;
+    if (gr < n) {
+      double g = 0.0;
+      for (int t = 0; t < 16; ++t) g = fmax(g, red[tid][t]);
+      double bound = 0.0;
+      for (int j = 0; j < m; ++j) bound = fma(fabs(rows[gr * m + j]), amax[j], bound);
+      bound *= kGradeRelErr;
+      gamma[gr] = g;
+      flags[gr] = (uint8_t)((g > tau_sel ? 1 : 0) | (g > tau_brk ? 2 : 0));
+      if (fabs(g - tau_sel) <= bound || fabs(g - tau_brk) <= bound) atomicAdd(n_ambiguous, 1ull);
+      atomicMax(gmax_bits, (unsigned long long)__double_as_longlong(g));
+    }
+  }
+}
+
+// max_k |A_jk| for every row j.
+__global__ void row_absmax_kernel(const double* __restrict__ a, int m, double* __restrict__ out) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= m) return;
+  double mx = 0.0;
+  for (int k = 0; k < m; ++k) mx = fmax(mx, fabs(a[(int64_t)j * m + k]));
+  out[j] = mx;
+}
+
+// Configuration mode: gamma_cfg = max_k |(bsum A_cfg^-1)_k| and its bound.
+__global__ void cfg_grade_kernel(const double* __restrict__ bsum, const double* __restrict__ acfg, int m,
+                                 double* __restrict__ out) {
+  __shared__ double smax[256], sbound[256];
+  double mx = 0.0, bd = 0.0;
+  for (int k = threadIdx.x; k < m; k += blockDim.x) {
+    double g = 0.0, b = 0.0;
+    for (int j = 0; j < m; ++j) {
+      g = fma(bsum[j], acfg[(int64_t)j * m + k], g);
+      b = fma(fabs(bsum[j]), fabs(acfg[(int64_t)j * m + k]), b);
+    }
+    mx = fmax(mx, fabs(g));
+    bd = fmax(bd, b);
+  }
+  smax[threadIdx.x] = mx;
+  sbound[threadIdx.x] = bd;
+  __syncthreads();
+  for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+    if (threadIdx.x < s) {
+      smax[threadIdx.x] = fmax(smax[threadIdx.x], smax[threadIdx.x + s]);
+      sbound[threadIdx.x] = fmax(sbound[threadIdx.x], sbound[threadIdx.x + s]);
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    out[0] = smax[0];
+    out[1] = kGradeRelErr * sbound[0];
+  }
+}
+
+}  // namespace mtp
+
+using namespace mtp;
+
+extern "C" int mtp_compute_grade(mtp_handle* h, const mtp_nlist* nl, const double* x, const int32_t* z, int64_t n,
+                                 const double* cell, const double* a_inv, const double* a_inv_cfg, double tau_sel,
+                                 double tau_brk, int64_t chunk_atoms, double* gamma, uint8_t* flags,
+                                 double* gamma_max, double* gamma_cfg, int64_t* n_ambiguous, void* stream) {
+  if (!h || !nl || !cell || (n > 0 && (!x || !z))) {
+    set_error("mtp_compute_grade: NULL argument");
+    return MTP_ERR_ARG;
+  }
+  if (n != nl->n_atoms) {
+    set_error("mtp_compute_grade: n_atoms = %lld but the list holds %lld", (long long)n, (long long)nl->n_atoms);
+    return MTP_ERR_ARG;
+  }
+  if (!a_inv && !a_inv_cfg) {
+    set_error("mtp_compute_grade: neither a neighbourhood nor a configuration active set was given");
+    return MTP_ERR_ARG;
+  }
+  if (a_inv && (!gamma || !flags)) {
+    set_error("mtp_compute_grade: neighbourhood mode needs gamma and flags outputs");
+    return MTP_ERR_ARG;
+  }
+  if (!(tau_sel > 0.0) || !(tau_brk >= tau_sel)) {
+    set_error("mtp_compute_grade: thresholds must satisfy 0 < tau_sel <= tau_brk");
+    return MTP_ERR_ARG;
+  }
+  if (chunk_atoms < 0) {
+    set_error("mtp_compute_grade: chunk_atoms < 0");
+    return MTP_ERR_ARG;
+  }
+  if (!h->ops->rows) {
+    set_error("mtp_compute_grade: level %d has no basis-row kernel", h->level);
+    return MTP_ERR_UNSUPPORTED;
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  const int m = h->m;
+  const int64_t chunk = chunk_atoms > 0 ? std::min<int64_t>(chunk_atoms, std::max<int64_t>(n, 1))
+                                        : std::min<int64_t>(std::max<int64_t>(n, 1), 262144);
+  int rc;
+  // scratch: [gmax bits, ambiguous count, cfg(2)] | amax [m] | bsum [m] | rows [chunk][m]
+  const size_t head = 8;
+  if ((rc = h->grade.ensure(sizeof(double) * (head + 2 * (size_t)m + (size_t)chunk * m))) != MTP_OK) return rc;
+  double* base = h->grade.as<double>();
+  unsigned long long* gmax_bits = reinterpret_cast<unsigned long long*>(base);
+  unsigned long long* n_amb = gmax_bits + 1;
+  double* cfg_out = base + 2;
+  double* amax = base + head;
+  double* bsum = amax + m;
+  double* rows = bsum + m;
+  MTP_TRY_CUDA(cudaMemsetAsync(base, 0, sizeof(double) * (head + 2 * (size_t)m), s));
+  if (a_inv) {
+    row_absmax_kernel<<<(m + 127) / 128, 128, 0, s>>>(a_inv, m, amax);
+    MTP_TRY_CUDA(cudaGetLastError());
+  }
+  EfvArgs a;
+  std::memset(&a, 0, sizeof(a));
+  a.n_atoms = n;
+  a.offsets = nl->offsets.as<int64_t>();
+  a.nbr_j = nl->nbr_j.as<int32_t>();
+  a.nbr_img = nl->nbr_img.as<int32_t>();
+  a.x = x;
+  a.z = z;
+  for (int k = 0; k < 9; ++k) {
+    a.cell[k] = cell[k];
+    a.cellf[k] = (float)cell[k];
+  }
+  a.n_species = h->n_species;
+  a.n_q = h->n_q;
+  a.n_mu = h->n_mu;
+  a.m = m;
+  a.r_min = h->r_min;
+  a.r_cut = h->r_cut;
+  a.radial_d = h->radial_d.as<double>();
+  a.xi_d = h->xi_d.as<double>();
+  a.status = h->status.as<int>();
+  for (int64_t b = 0; b < n; b += chunk) {
+    const int64_t cnt = std::min<int64_t>(chunk, n - b);
+    a.atom_begin = b;
+    a.atom_end = b + cnt;
+    if ((rc = h->ops->rows(a, nullptr, cnt, rows, m, a_inv_cfg ? bsum : nullptr, s)) != MTP_OK) return rc;
+    if (a_inv) {
+      gemm_grade_kernel<<<(unsigned)((cnt + kGemmBM - 1) / kGemmBM), 256, 0, s>>>(
+          rows, cnt, m, a_inv, amax, tau_sel, tau_brk, gamma + b, flags + b, gmax_bits, n_amb);
+      MTP_TRY_CUDA(cudaGetLastError());
+    }
+  }
+  if (a_inv_cfg) {
+    cfg_grade_kernel<<<1, 256, 0, s>>>(bsum, a_inv_cfg, m, cfg_out);
+    MTP_TRY_CUDA(cudaGetLastError());
+  }
+  double hostbuf[4] = {0, 0, 0, 0};
+  MTP_TRY_CUDA(cudaMemcpyAsync(hostbuf, base, sizeof(double) * 4, cudaMemcpyDeviceToHost, s));
+  MTP_TRY_CUDA(cudaStreamSynchronize(s));
+  unsigned long long gbits, amb;
+  std::memcpy(&gbits, &hostbuf[0], sizeof(gbits));
+  std::memcpy(&amb, &hostbuf[1], sizeof(amb));
+  double gmax;
+  std::memcpy(&gmax, &gbits, sizeof(gmax));
+  if (a_inv_cfg && std::fabs(hostbuf[2] - tau_sel) <= hostbuf[3]) ++amb;
+  if (a_inv_cfg && std::fabs(hostbuf[2] - tau_brk) <= hostbuf[3]) ++amb;
+  if (gamma_max) *gamma_max = a_inv ? gmax : 0.0;
+  if (gamma_cfg) *gamma_cfg = a_inv_cfg ? hostbuf[2] : 0.0;
+  if (n_ambiguous) *n_ambiguous = (int64_t)amb;
+  if (!std::isfinite(gmax) || (a_inv_cfg && !std::isfinite(hostbuf[2]))) {
+    set_error("mtp_compute_grade: non-finite grade");
+    return MTP_ERR_NONFINITE;
+  }
+  const double worst = std::max(a_inv ? gmax : 0.0, a_inv_cfg ? hostbuf[2] : 0.0);
+  return worst > tau_brk ? MTP_STATUS_BREAK : MTP_OK;
+}

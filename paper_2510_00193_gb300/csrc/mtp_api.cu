@@ -230,6 +230,7 @@ void mtp_free(mtp_handle* h) {
   h->status.release();
   h->xq.release();
   h->forces_f.release();
+  h->grade.release();
   delete h;
 }
 

@@ -2,6 +2,7 @@
 #pragma once
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cstdint>
 #include <vector>
 
@@ -72,10 +73,18 @@ struct EfvArgs {
 };
 
 using EfvLaunch = int (*)(const EfvArgs&, int precision, bool want_dtheta, cudaStream_t);
+// FP64 basis rows of listed atoms (list == nullptr: atoms atom_begin..), optional FP64 column sums.
+using RowsLaunch = int (*)(const EfvArgs&, const int32_t* list, int64_t n_rows, double* rows, int64_t ld,
+                           double* bsum, cudaStream_t);
+
+struct BatchArgs;
+using BatchLaunch = int (*)(const BatchArgs&, int precision, bool want_dtheta, int threads, cudaStream_t);
 
 struct LevelEntry {
   int level;
   EfvLaunch efv;
+  RowsLaunch rows;
+  BatchLaunch batch;
   int shmem_bytes_max;
 };
 
@@ -93,6 +102,7 @@ struct mtp_handle {
   mtp::DevBuf species, radial_d, xi_d, radial_f, xi_f, status;
   mtp::DevBuf xq;        // fixed-point positions scratch
   mtp::DevBuf forces_f;  // FP32 force accumulator (mixed path)
+  mtp::DevBuf grade;     // grade scratch: counters, row maxima, column sums, FP64 basis rows
 };
 
 struct mtp_nlist {

@@ -91,41 +91,65 @@ def random_triclinic_cell(n_atoms: int, density: float, g: np.random.Generator) 
     return h
 
 
-def _min_image_dist2(dx: np.ndarray, cell: np.ndarray, reach: int) -> np.ndarray:
-    """Smallest squared length of dx + n.cell over integer n in [-reach, reach]^3."""
-    best = np.full(dx.shape[0], np.inf)
-    r = range(-reach, reach + 1)
-    for n1 in r:
-        for n2 in r:
-            for n3 in r:
-                s = n1 * cell[0] + n2 * cell[1] + n3 * cell[2]
-                d = dx + s
-                best = np.minimum(best, np.einsum("ij,ij->i", d, d))
-    return best
+def _image_shifts(cell: np.ndarray, reach: int) -> np.ndarray:
+    r = np.arange(-reach, reach + 1)
+    n = np.stack(np.meshgrid(r, r, r, indexing="ij"), -1).reshape(-1, 3).astype(np.float64)
+    return n @ cell
 
 
 def random_gas(n_atoms: int, density: float, min_sep: float, n_species: int, g: np.random.Generator,
-               max_attempts: int = 200000) -> Structure | None:
+               max_attempts: int = 400000, chunk: int = 256) -> Structure | None:
     """Random sequential insertion in a random triclinic cell, rejecting any
     trial point closer than ``min_sep`` to an accepted one under every
-    periodic image.  Returns None if the attempt budget runs out."""
+    periodic image.  Trial points are drawn ``chunk`` at a time (the same
+    sequence as one at a time).  Distances use the fractional difference
+    wrapped to [-0.5, 0.5] plus the images n in [-R, R]^3 with
+    R = floor(0.5 + min_sep / h_min), h_min the smallest plane spacing: every
+    image closer than min_sep lies in that set.  Returns None if the attempt
+    budget runs out."""
     cell = random_triclinic_cell(n_atoms, density, g)
     inv = np.linalg.inv(cell)
     heights = 1.0 / np.linalg.norm(inv, axis=0)
-    reach = int(math.ceil(min_sep / heights.min())) + 1
-    pts = np.zeros((0, 3))
+    reach = int(math.floor(0.5 + min_sep / heights.min()))
+    r = np.arange(-reach, reach + 1)
+    imgs = np.stack(np.meshgrid(r, r, r, indexing="ij"), -1).reshape(-1, 3).astype(np.float64)
+    lim = min_sep * min_sep
+    acc = np.zeros((n_atoms, 3))        # fractional coordinates of accepted points
+    count = 0
     attempts = 0
-    while pts.shape[0] < n_atoms:
-        attempts += 1
-        if attempts > max_attempts:
+
+    def dist2(tr, pts):
+        d = tr[:, None, :] - pts[None, :, :]
+        d -= np.round(d)
+        v = (d[:, :, None, :] + imgs[None, None, :, :]) @ cell
+        return np.einsum("tpsk,tpsk->tps", v, v).min(axis=(1, 2))
+
+    while count < n_atoms:
+        if attempts >= max_attempts:
             return None
-        p = g.uniform(0.0, 1.0, size=3) @ cell
-        if pts.shape[0]:
-            if _min_image_dist2(pts - p, cell, reach).min() < min_sep * min_sep:
+        trials = g.uniform(0.0, 1.0, size=(chunk, 3))
+        best = dist2(trials, acc[:count]) if count else np.full(chunk, np.inf)
+        for t in range(chunk):
+            attempts += 1
+            if best[t] < lim:
                 continue
-        pts = np.vstack([pts, p])
+            acc[count] = trials[t]
+            count += 1
+            if count == n_atoms or attempts >= max_attempts:
+                break
+            if t + 1 < chunk:
+                best[t + 1:] = np.minimum(best[t + 1:], dist2(trials[t + 1:], trials[t:t + 1]))
     z = balanced_species(n_atoms, n_species, g)
-    return Structure(wrap(pts, cell), z, cell)
+    return Structure(wrap(acc @ cell, cell), z, cell)
+
+
+def _gas_job(args):
+    stream, k, n, density, min_sep, n_species = args
+    gk = rng(stream, 1000 + k)
+    s = None
+    while s is None:
+        s = random_gas(int(n), density, min_sep, n_species, gk)
+    return s
 
 
 def batch_sizes(n_cfg: int, lo: int, hi: int, g: np.random.Generator) -> np.ndarray:
@@ -134,19 +158,22 @@ def batch_sizes(n_cfg: int, lo: int, hi: int, g: np.random.Generator) -> np.ndar
 
 
 def random_gas_batch(n_cfg: int, lo: int, hi: int, density: float, min_sep: float, n_species: int,
-                     stream: int) -> list[Structure]:
-    """Batch of random periodic gases with log-uniform sizes; each failed
-    insertion is redrawn from the same sub-stream."""
+                     stream: int, workers: int = 0) -> list[Structure]:
+    """Batch of random periodic gases with log-uniform sizes; each
+    configuration has its own sub-stream, and a failed insertion is redrawn
+    from it.  ``workers`` > 1 generates in that many spawned processes (the
+    result does not depend on it); 0 = one per CPU core for large batches."""
     g = rng(stream, 30)
     sizes = batch_sizes(n_cfg, lo, hi, g)
-    out = []
-    for k, n in enumerate(sizes):
-        gk = rng(stream, 1000 + k)
-        s = None
-        while s is None:
-            s = random_gas(int(n), density, min_sep, n_species, gk)
-        out.append(s)
-    return out
+    jobs = [(stream, k, int(n), density, min_sep, n_species) for k, n in enumerate(sizes)]
+    if workers == 0:
+        import os
+        workers = (os.cpu_count() or 1) if n_cfg >= 64 else 1
+    if workers <= 1:
+        return [_gas_job(j) for j in jobs]
+    import multiprocessing as mp
+    with mp.get_context("spawn").Pool(workers) as pool:
+        return pool.map(_gas_job, jobs, chunksize=max(1, n_cfg // (8 * workers)))
 
 
 @dataclasses.dataclass
