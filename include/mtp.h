@@ -131,6 +131,17 @@ int mtp_compute_efv(mtp_handle* h, const mtp_nlist* nl, const double* x_dev, con
                     double* e_atom_dev, double* forces_dev, double* virial_dev, double* e_total_dev,
                     double* dEdtheta_dev, void* stream);
 
+/* Directional second derivatives, for the parameter gradient of a loss on
+ * forces (double backward): with v_dev (DEVICE [N][3]) a direction of the
+ * positions, dtheta_tan_dev [n_params] = d/dt dE/dtheta (x + t v) and
+ * force_tan_dev [N][3] (nullable) = d/dt F(x + t v) = -H v.  For a
+ * force-matching loss l = (1/3N) sum |F - F_t|^2 with v = F - F_t,
+ * dl/dtheta = -(2/3N) dtheta_tan.  Forward-mode (dual-number) evaluation of
+ * the energy/force code; species-energy entries are zero.  Asynchronous. */
+int mtp_compute_efv_tangent(mtp_handle* h, const mtp_nlist* nl, const double* x_dev, const int32_t* z_dev,
+                            int64_t n_atoms, const double* cell, int32_t precision, const double* v_dev,
+                            double* dtheta_tan_dev, double* force_tan_dev, void* stream);
+
 /* Extrapolation grade (paper Sec. 2.1: configuration and neighbourhood mode
  * with a selection and a break threshold; Sec. 2.3: select above tau_sel,
  * halt above tau_brk).  With b_i the basis row of atom i (the m basis

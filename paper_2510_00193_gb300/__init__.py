@@ -19,7 +19,7 @@ from ._lib import MTP_FP64, MTP_MIXED, MtpError, check
 __all__ = [
     "MTP_FP64", "MTP_MIXED", "MtpError", "Potential", "NeighborList", "mtp_basis_info", "mtp_basis_table",
     "mtp_load_params", "mtp_build_neighbors", "mtp_compute_efv", "mtp_compute_efv_noalloc", "mtp_compute_grade",
-    "mtp_device_status", "Batch", "mtp_batch_create", "mtp_compute_batch", "mtp_batch_tune",
+    "mtp_device_status", "mtp_compute_efv_tangent", "Batch", "mtp_batch_create", "mtp_compute_batch", "mtp_batch_tune",
     "library_path",
 ]
 
@@ -369,6 +369,23 @@ def mtp_batch_tune(potential: Potential, batch: Batch, x, z, precision=MTP_MIXED
         int(precision), int(bool(dtheta)), ctypes.byref(chosen), _dptr(out["e_cfg"]), _dptr(out["forces"]),
         _dptr(out["virial"]), _dptr(out["dtheta"]) if dtheta else None, _stream_ptr(stream)))
     return chosen.value
+
+
+def mtp_compute_efv_tangent(potential: Potential, nlist: NeighborList, x, z, cell, v, precision=MTP_FP64,
+                            force_tan=True, stream=None) -> dict:
+    """Directional second derivatives along v ([N, 3] float64 CUDA tensor):
+    dtheta_tan = d/dt dE/dtheta (x + t v) and force_tan = d/dt F(x + t v)."""
+    import torch
+    n = x.shape[0]
+    out = {"dtheta_tan": torch.empty(potential.n_params, dtype=torch.float64, device=x.device),
+           "force_tan": torch.empty((n, 3), dtype=torch.float64, device=x.device) if force_tan else None}
+    c = _host_d(cell, 9)
+    check(_lib.load().mtp_compute_efv_tangent(
+        potential.handle, nlist.handle, _dptr(x, torch.float64, 3 * n, "x"), _dptr(z, torch.int32, n, "z"), n,
+        c.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), int(precision), _dptr(v, torch.float64, 3 * n, "v"),
+        _dptr(out["dtheta_tan"], torch.float64, potential.n_params, "dtheta_tan"),
+        _dptr(out["force_tan"], torch.float64, 3 * n, "force_tan") if force_tan else None, _stream_ptr(stream)))
+    return out
 
 
 def mtp_device_status(potential: Potential, stream=None) -> int:

@@ -59,6 +59,7 @@ SIGNATURES = {
     "mtp_nlist_copy": (ctypes.c_int, [_VP, _VP, _VP, _VP, _VP]),
     "mtp_free_nlist": (None, [_VP]),
     "mtp_compute_efv": (ctypes.c_int, [_VP, _VP, _VP, _VP, _I64, _P_D, _I32, _I64, _VP, _VP, _VP, _VP, _VP, _VP]),
+    "mtp_compute_efv_tangent": (ctypes.c_int, [_VP, _VP, _VP, _VP, _I64, _P_D, _I32, _VP, _VP, _VP, _VP]),
     "mtp_compute_grade": (ctypes.c_int, [_VP, _VP, _VP, _VP, _I64, _P_D, _VP, _VP, ctypes.c_double, ctypes.c_double,
                                          _I64, _VP, _VP, _P_D, _P_D, _P_I64, _VP]),
     "mtp_batch_create": (ctypes.c_int, [_VP, _I32, _P_I64, _P_D, _P_I32, _VP, _I32, ctypes.POINTER(_VP), _VP]),

@@ -63,6 +63,7 @@ def generate_sources(levels=LEVELS):
         _write(path, (
             "// Generated by paper_2510_00193_gb300/build.py.\n"
             "#include \"efv_kernel.cuh\"\n#include \"grade_kernel.cuh\"\n#include \"batch_kernel.cuh\"\n"
+            "#include \"tangent_kernel.cuh\"\n"
             "#include \"mtp_level%d.cuh\"\n"
             "namespace mtp {\nint efv_level%d(const EfvArgs& a, int precision, bool want_dtheta, cudaStream_t s) {\n"
             "  return efv_launch<MtpLevel%d>(a, precision, want_dtheta, s);\n}\n"
@@ -70,13 +71,17 @@ def generate_sources(levels=LEVELS):
             " cudaStream_t s) {\n  return basis_rows_launch<MtpLevel%d>(a, list, n, rows, ld, bsum, s);\n}\n"
             "int batch_level%d(const BatchArgs& b, int precision, bool want_dtheta, int threads, cudaStream_t s) {\n"
             "  return batch_launch<MtpLevel%d>(b, precision, want_dtheta, threads, s);\n}\n"
-            "}  // namespace mtp\n") % (L, L, L, L, L, L, L))
+            "int tangent_level%d(const TangentArgs& t, int precision, cudaStream_t s) {\n"
+            "  return tangent_launch<MtpLevel%d>(t, precision, s);\n}\n"
+            "}  // namespace mtp\n") % (L, L, L, L, L, L, L, L, L))
         units.append(path)
     decl = "".join("int efv_level%d(const EfvArgs&, int, bool, cudaStream_t);\n"
                    "int rows_level%d(const EfvArgs&, const int32_t*, int64_t, double*, int64_t, double*, cudaStream_t);\n"
                    "int batch_level%d(const BatchArgs&, int, bool, int, cudaStream_t);\n"
-                   % (L, L, L) for L in levels)
-    table = ",\n".join("  {%d, efv_level%d, rows_level%d, batch_level%d, 0}" % (L, L, L, L) for L in levels)
+                   "int tangent_level%d(const TangentArgs&, int, cudaStream_t);\n"
+                   % (L, L, L, L) for L in levels)
+    table = ",\n".join("  {%d, efv_level%d, rows_level%d, batch_level%d, tangent_level%d, 0}" % (L, L, L, L, L)
+                        for L in levels)
     reg = os.path.join(GEN, "levels.cu")
     _write(reg, (
         "// Generated by paper_2510_00193_gb300/build.py.\n#include \"mtp_internal.cuh\"\nnamespace mtp {\n%s"

@@ -173,9 +173,10 @@ __device__ __forceinline__ double rsqrt_r(double v) { return rsqrt(v); }
 // Radial functions of one pair.  c points at the (zi, zj) block, [mu][k].
 // f_mu = cut^2 sum_k c T_k, df_mu/dr = scale cut^2 sum_k c T'_k - 2 cut sum_k c T_k,
 // with T_k(xi) the Chebyshev polynomials, xi = (r - mid) scale, cut = R_cut - r.
-template <class R, int NMU, bool DERIV, bool WANT_Q>
-__device__ __forceinline__ void radial(const R* __restrict__ c, int nq, R r, R mid, R scale, R rcut, R* f,
+template <class R, int NMU, bool DERIV, bool WANT_Q, class C>
+__device__ __forceinline__ void radial(const C* __restrict__ c, int nq, R r, R mid, R scale, R rcut, R* f,
                                        R* df, R* q) {
+  // c holds scalar coefficients (C); R may be C or a dual number over C
   const R x = (r - mid) * scale;
   const R cut = rcut - r;
   const R cut2 = cut * cut;
@@ -183,15 +184,15 @@ __device__ __forceinline__ void radial(const R* __restrict__ c, int nq, R r, R m
   R A[NMU], Bd[NMU];
 #pragma unroll
   for (int mu = 0; mu < NMU; ++mu) {
-    A[mu] = c[mu * nq];
+    A[mu] = R(c[mu * nq]);
     Bd[mu] = R(0);
   }
   if (WANT_Q) q[0] = cut2;
   if (nq > 1) {
 #pragma unroll
     for (int mu = 0; mu < NMU; ++mu) {
-      A[mu] = fmadd(c[mu * nq + 1], x, A[mu]);
-      if (DERIV) Bd[mu] = c[mu * nq + 1];
+      A[mu] = fmadd(R(c[mu * nq + 1]), x, A[mu]);
+      if (DERIV) Bd[mu] = R(c[mu * nq + 1]);
     }
     if (WANT_Q) q[1] = x * cut2;
   }
@@ -202,7 +203,7 @@ __device__ __forceinline__ void radial(const R* __restrict__ c, int nq, R r, R m
       const R d2 = fmadd(R(2) * x, d1, fmadd(R(2), t1, -d0));
 #pragma unroll
       for (int mu = 0; mu < NMU; ++mu) {
-        const R cc = c[mu * nq + k];
+        const R cc = R(c[mu * nq + k]);
         A[mu] = fmadd(cc, t2, A[mu]);
         if (DERIV) Bd[mu] = fmadd(cc, d2, Bd[mu]);
       }
@@ -322,6 +323,15 @@ __device__ __forceinline__ void efv_atom(const EfvArgs& a, const EfvShared<R, LV
   a.e_atom[i] = e_i;
 
   R fx = R(0), fy = R(0), fz = R(0);
+  // dE/dc contributions of this atom's pairs, summed per neighbour species in
+  // thread-private memory and added to the block's shared accumulators once
+  // per atom (per-pair shared atomics collide heavily between lanes)
+  constexpr int kAccS = 4;
+  const bool own_acc = DTHETA && sm.S <= kAccS;
+  R acc[DTHETA ? kAccS * NMU * kMaxQ : 1];
+  if (own_acc) {
+    for (int t = 0; t < sm.S * NMU * kMaxQ; ++t) acc[t] = R(0);
+  }
   ps.start(a, geom, beg, end);
   while (ps.next(a, geom, j, img, lj)) {
     const int zj = lj.species;
@@ -343,13 +353,30 @@ __device__ __forceinline__ void efv_atom(const EfvArgs& a, const EfvShared<R, LV
     w[4] = fmadd(R(-0.5), fmadd(gx, dz, gz * dx), w[4]);
     w[5] = fmadd(R(-0.5), fmadd(gy, dz, gz * dy), w[5]);
     if (DTHETA) {
-      R* dst = sm.dc + (zi * sm.S + zj) * NMU * sm.nq;
+      if (own_acc) {
+        R* dst = acc + zj * NMU * kMaxQ;
 #pragma unroll
-      for (int mu = 0; mu < NMU; ++mu) {
+        for (int mu = 0; mu < NMU; ++mu) {
 #pragma unroll
-        for (int kk = 0; kk < kMaxQ; ++kk)
-          if (kk < sm.nq) atomicAdd(dst + mu * sm.nq + kk, q[kk] * Smu[mu]);
+          for (int kk = 0; kk < kMaxQ; ++kk)
+            if (kk < sm.nq) dst[mu * kMaxQ + kk] = fmadd(q[kk], Smu[mu], dst[mu * kMaxQ + kk]);
+        }
+      } else {
+        R* dst = sm.dc + (zi * sm.S + zj) * NMU * sm.nq;
+#pragma unroll
+        for (int mu = 0; mu < NMU; ++mu) {
+#pragma unroll
+          for (int kk = 0; kk < kMaxQ; ++kk)
+            if (kk < sm.nq) atomicAdd(dst + mu * sm.nq + kk, q[kk] * Smu[mu]);
+        }
       }
+    }
+  }
+  if (own_acc) {
+    for (int zj = 0; zj < sm.S; ++zj) {
+      R* dst = sm.dc + (zi * sm.S + zj) * NMU * sm.nq;
+      for (int mu = 0; mu < NMU; ++mu)
+        for (int kk = 0; kk < sm.nq; ++kk) atomicAdd(dst + mu * sm.nq + kk, acc[(zj * NMU + mu) * kMaxQ + kk]);
     }
   }
   scatter_force(a, i, fx, fy, fz);

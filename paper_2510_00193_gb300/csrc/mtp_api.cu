@@ -9,6 +9,7 @@
 
 #include "mtp_internal.cuh"
 #include "mtp_tables.h"
+#include "tangent_kernel.cuh"
 
 namespace mtp {
 
@@ -451,3 +452,93 @@ int mtp_device_status(mtp_handle* h, void* stream) {
 }
 
 }  // extern "C"
+
+namespace mtp {
+static int fill_efv_args(mtp_handle* h, const mtp_nlist* nl, const double* x, const int32_t* z, int64_t n,
+                         const double* cell, EfvArgs& a) {
+  std::memset(&a, 0, sizeof(a));
+  a.n_atoms = n;
+  a.offsets = nl->offsets.as<int64_t>();
+  a.nbr_j = nl->nbr_j.as<int32_t>();
+  a.nbr_img = nl->nbr_img.as<int32_t>();
+  a.x = x;
+  a.z = z;
+  for (int k = 0; k < 9; ++k) {
+    a.cell[k] = cell[k];
+    a.cellf[k] = (float)cell[k];
+  }
+  a.n_species = h->n_species;
+  a.n_q = h->n_q;
+  a.n_mu = h->n_mu;
+  a.m = h->m;
+  a.r_min = h->r_min;
+  a.r_cut = h->r_cut;
+  a.species_energy = h->species.as<double>();
+  a.radial_d = h->radial_d.as<double>();
+  a.xi_d = h->xi_d.as<double>();
+  a.radial_f = h->radial_f.as<float>();
+  a.xi_f = h->xi_f.as<float>();
+  a.status = h->status.as<int>();
+  return MTP_OK;
+}
+}  // namespace mtp
+
+extern "C" int mtp_compute_efv_tangent(mtp_handle* h, const mtp_nlist* nl, const double* x, const int32_t* z,
+                                       int64_t n, const double* cell, int32_t precision, const double* v,
+                                       double* dtheta_tan, double* force_tan, void* stream) {
+  if (!h || !nl || !cell || !dtheta_tan || (n > 0 && (!x || !z || !v))) {
+    set_error("mtp_compute_efv_tangent: NULL argument");
+    return MTP_ERR_ARG;
+  }
+  if (n != nl->n_atoms) {
+    set_error("mtp_compute_efv_tangent: n_atoms = %lld but the list holds %lld", (long long)n,
+              (long long)nl->n_atoms);
+    return MTP_ERR_ARG;
+  }
+  if (precision != MTP_FP64 && precision != MTP_MIXED) {
+    set_error("mtp_compute_efv_tangent: precision must be MTP_FP64 or MTP_MIXED");
+    return MTP_ERR_ARG;
+  }
+  if (!h->ops->tangent) {
+    set_error("mtp_compute_efv_tangent: level %d has no tangent kernel", h->level);
+    return MTP_ERR_UNSUPPORTED;
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  MTP_TRY_CUDA(cudaMemsetAsync(dtheta_tan, 0, sizeof(double) * h->n_params, s));
+  if (force_tan) MTP_TRY_CUDA(cudaMemsetAsync(force_tan, 0, sizeof(double) * 3 * (size_t)n, s));
+  if (n == 0) return MTP_OK;
+  TangentArgs t;
+  std::memset(&t, 0, sizeof(t));
+  fill_efv_args(h, nl, x, z, n, cell, t.base);
+  t.v = v;
+  t.dtheta_tan = dtheta_tan;
+  t.force_tan = force_tan;
+  if (precision == MTP_MIXED) {
+    int rc = h->xq.ensure(sizeof(long long) * 4 * (size_t)n);
+    if (rc != MTP_OK) return rc;
+    double det = cell[0] * (cell[4] * cell[8] - cell[5] * cell[7]) - cell[1] * (cell[3] * cell[8] - cell[5] * cell[6]) +
+                 cell[2] * (cell[3] * cell[7] - cell[4] * cell[6]);
+    if (!(std::fabs(det) > 0.0)) {
+      set_error("mtp_compute_efv_tangent: singular cell");
+      return MTP_ERR_ARG;
+    }
+    double hi[9];
+    hi[0] = (cell[4] * cell[8] - cell[5] * cell[7]) / det;
+    hi[1] = (cell[2] * cell[7] - cell[1] * cell[8]) / det;
+    hi[2] = (cell[1] * cell[5] - cell[2] * cell[4]) / det;
+    hi[3] = (cell[5] * cell[6] - cell[3] * cell[8]) / det;
+    hi[4] = (cell[0] * cell[8] - cell[2] * cell[6]) / det;
+    hi[5] = (cell[2] * cell[3] - cell[0] * cell[5]) / det;
+    hi[6] = (cell[3] * cell[7] - cell[4] * cell[6]) / det;
+    hi[7] = (cell[1] * cell[6] - cell[0] * cell[7]) / det;
+    hi[8] = (cell[0] * cell[4] - cell[1] * cell[3]) / det;
+    fixed_point_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(x, z, n, hi[0], hi[1], hi[2], hi[3], hi[4], hi[5],
+                                                                   hi[6], hi[7], hi[8], h->n_species,
+                                                                   h->xq.as<long long>(), t.base.status);
+    MTP_TRY_CUDA(cudaGetLastError());
+    t.base.xq = h->xq.as<long long>();
+  }
+  t.base.atom_begin = 0;
+  t.base.atom_end = n;
+  return h->ops->tangent(t, precision, s);
+}

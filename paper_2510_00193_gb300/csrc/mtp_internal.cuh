@@ -79,12 +79,15 @@ using RowsLaunch = int (*)(const EfvArgs&, const int32_t* list, int64_t n_rows, 
 
 struct BatchArgs;
 using BatchLaunch = int (*)(const BatchArgs&, int precision, bool want_dtheta, int threads, cudaStream_t);
+struct TangentArgs;
+using TangentLaunch = int (*)(const TangentArgs&, int precision, cudaStream_t);
 
 struct LevelEntry {
   int level;
   EfvLaunch efv;
   RowsLaunch rows;
   BatchLaunch batch;
+  TangentLaunch tangent;
   int shmem_bytes_max;
 };
 

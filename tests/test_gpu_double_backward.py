@@ -1,0 +1,83 @@
+"""Force-matching double backward through torch.autograd over the C-ABI:
+d loss / d theta with loss = (1/3N) sum |F - F_t|^2, F = -dE/dx, against the
+oracle's double backward (FP64, 1e-8 relative to the largest entry), the
+Hessian-vector product against central differences of the GPU forces, and
+the mixed-precision path with its error stated against the FP64 result."""
+import numpy as np
+import pytest
+
+import synth
+from oracle import mtp as O
+from tests.helpers import oracle_model, pot_dict, structure
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def P():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2510_00193_gb300 import build as B
+    B.build()
+    import paper_2510_00193_gb300 as P
+    return P
+
+
+CASES = {
+    "bcc-l8-s1": ("bcc", (3, 3, 3), 3.16, 0.1, 1, 1),
+    "bcc-l16-s3": ("bcc", (3, 3, 2), 3.16, 0.1, 3, 2),
+}
+
+
+def gpu_loss_grad(P, name, st, ft, precision):
+    from paper_2510_00193_gb300.autograd import energy
+    pot = P.Potential.from_dict(pot_dict(name))
+    x = torch.tensor(st.x, dtype=torch.float64, device="cuda", requires_grad=True)
+    z = torch.tensor(st.z, device="cuda")
+    nl = P.mtp_build_neighbors(pot, x.detach(), st.cell, st.pbc)
+    theta = torch.zeros(pot.n_params, dtype=torch.float64, device="cuda", requires_grad=True)
+    e = energy(pot, nl, x, z, st.cell, theta, precision)
+    (gx,) = torch.autograd.grad(e, x, create_graph=True)
+    f = -gx
+    loss = ((f - torch.tensor(ft, device="cuda")) ** 2).sum() / (3 * st.n)
+    loss.backward()
+    return loss.item(), theta.grad.cpu().numpy(), pot, nl, x, z
+
+
+@pytest.mark.parametrize("name", sorted(CASES))
+def test_force_matching_gradient_matches_oracle(P, name):
+    st = structure(*CASES[name])
+    ft = synth.target_forces(st.n, 9)
+    loss, g, *_ = gpu_loss_grad(P, name, st, ft, P.MTP_FP64)
+    model = oracle_model(name)
+    nl = O.neighbor_list(st.x, st.cell, st.pbc, pot_dict(name)["r_cut"])
+    loss_ref, grads = O.force_matching_grad(model, st.x, st.z, st.cell, nl, ft)
+    ref = np.concatenate([grads[0], grads[1].ravel(), grads[2]])
+    assert loss == pytest.approx(loss_ref, rel=1e-10)
+    assert np.abs(g - ref).max() <= 1e-8 * np.abs(ref).max()
+    # mixed precision: same gradient within 1e-4 of the largest entry
+    _, gm, *_ = gpu_loss_grad(P, name, st, ft, P.MTP_MIXED)
+    assert np.abs(gm - ref).max() <= 1e-4 * np.abs(ref).max()
+
+
+def test_hessian_vector_product_matches_finite_differences(P):
+    name = "bcc-l16-s3"
+    st = structure(*CASES[name])
+    pot = P.Potential.from_dict(pot_dict(name))
+    z = torch.tensor(st.z, device="cuda")
+    v = synth.rng(3, 9).normal(size=st.x.shape)
+    x = torch.tensor(st.x, device="cuda")
+    nl = P.mtp_build_neighbors(pot, x, st.cell, st.pbc)
+    tan = P.mtp_compute_efv_tangent(pot, nl, x, z, st.cell, torch.tensor(v, device="cuda"), precision=P.MTP_FP64)
+    h = 1e-5
+    fp = P.mtp_compute_efv(pot, nl, torch.tensor(st.x + h * v, device="cuda"), z, st.cell, precision=P.MTP_FP64,
+                           dtheta=True)
+    fm = P.mtp_compute_efv(pot, nl, torch.tensor(st.x - h * v, device="cuda"), z, st.cell, precision=P.MTP_FP64,
+                           dtheta=True)
+    fd_f = (fp["forces"] - fm["forces"]).cpu().numpy() / (2 * h)
+    fd_t = (fp["dtheta"] - fm["dtheta"]).cpu().numpy() / (2 * h)
+    got_f = tan["force_tan"].cpu().numpy()
+    got_t = tan["dtheta_tan"].cpu().numpy()
+    assert np.abs(got_f - fd_f).max() <= 1e-5 * max(1.0, np.abs(fd_f).max())
+    assert np.abs(got_t - fd_t).max() <= 1e-5 * max(1.0, np.abs(fd_t).max())
