@@ -713,12 +713,79 @@ def emit_contract(lv: Level):
     return L
 
 
+INTERPRET_FROM_LEVEL = 18
+
+
+def emit_contract_program(lv: Level):
+    """Contraction as a program for a per-thread interpreter (levels whose
+    straight-line code would be too large).  Values V: [0, C) moment
+    components, then every DAG node component, a constant 1, the graph values
+    and the basis values.  Records (int32): DOT = [0, dst, n, (a, b, w) * n]
+    meaning V[dst] = sum w V[a] V[b]; PROD = [1, dst, n, g * n] meaning
+    V[dst] = prod V[g].  Forward runs the records in order, the reverse pass
+    in reverse order."""
+    dag = lv.dag
+    C = len(lv.comps)
+    base = {}
+    nv = C
+    for n, (key, rank) in enumerate(dag.nodes):
+        if key[0] == "C":
+            base[n] = nv
+            nv += n_sym(rank)
+    one = nv
+    nv += 1
+    goff = nv
+    nv += len(lv.graphs)
+    boff = nv
+    nv += lv.m
+
+    def ref(n, K):
+        key, rank = dag.nodes[n]
+        if key[0] == "M":
+            _, mu, nu, off = key
+            return lv.comp_index[(mu, (off[0] + K[0], off[1] + K[1], off[2] + K[2]))]
+        return base[n] + multi_indices(rank).index(K)
+
+    prog, starts = [], []
+    for n, (key, rank) in enumerate(dag.nodes):
+        if key[0] != "C":
+            continue
+        _, a, b = key
+        Ps = multi_indices(dag.rank(b))
+        for ki, K in enumerate(multi_indices(rank)):
+            starts.append(len(prog))
+            prog += [0, base[n] + ki, len(Ps)]
+            for P in Ps:
+                prog += [ref(a, (K[0] + P[0], K[1] + P[1], K[2] + P[2])), ref(b, P), multinomial_weight(P)]
+    for gi, roots in enumerate(lv.roots):
+        starts.append(len(prog))
+        prog += [0, goff + gi, len(roots)]
+        for w, node in roots:
+            prog += [ref(node, (0, 0, 0)), one, w]
+    for a_, bas in enumerate(lv.bases):
+        starts.append(len(prog))
+        prog += [1, boff + a_, len(bas)] + [goff + k for k in bas]
+    L = []
+    nm = "L%d" % lv.level
+    L.append("  static constexpr int NVALUES = %d, ONE = %d, BOFF = %d, NRECORDS = %d;" % (nv, one, boff, len(starts)))
+    L.append("  template <class R, bool WANT_B>")
+    L.append("  __device__ static R contract(const R* __restrict__ M, const typename ScalarOf<R>::T* __restrict__ xi, "
+             "R* __restrict__ D, R* __restrict__ B) {")
+    L.append("    return interpret_contract<R, WANT_B, NCOMP, NVALUES, ONE, BOFF, NBASIS, NRECORDS>("
+             "kProg%s, kStarts%s, M, xi, D, B);" % (nm, nm))
+    L.append("  }")
+    tables = ["__device__ const int32_t kProg%s[] = {%s};" % (nm, ",".join(str(v) for v in prog)),
+              "__device__ const int32_t kStarts%s[] = {%s};" % (nm, ",".join(str(v) for v in starts))]
+    return L, tables
+
+
 def emit_header(lv: Level):
     name = "MtpLevel%d" % lv.level
     out = []
     out.append("// Generated by paper_2510_00193_gb300/basisgen.py for MTP level %d. Do not edit." % lv.level)
     out.append("#pragma once")
     out.append("#include \"mtp_math.cuh\"")
+    out.append("#include \"mtp_interp.cuh\"")
     out.append("namespace mtp {")
     out.append("struct %s {" % name)
     out.append("  static constexpr int LEVEL = %d;" % lv.level)
@@ -729,7 +796,12 @@ def emit_header(lv: Level):
     out.append("  static constexpr int NUMAX = %d;" % max(lv.nu_max))
     out += emit_moments(lv)
     out += emit_pair_adjoint(lv)
-    out += emit_contract(lv)
+    if lv.level >= INTERPRET_FROM_LEVEL:
+        body, tables = emit_contract_program(lv)
+        out = out[:out.index("struct %s {" % name)] + tables + out[out.index("struct %s {" % name):]
+        out += body
+    else:
+        out += emit_contract(lv)
     out.append("};")
     out.append("}  // namespace mtp")
     return "\n".join(out) + "\n"

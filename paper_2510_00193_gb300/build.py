@@ -22,7 +22,7 @@ GEN = os.path.join(BUILD, "gen")
 LIB = os.path.join(HERE, "libmtp_gb300.so")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-LEVELS = (2, 4, 6, 8, 10, 12, 14, 16)
+LEVELS = (2, 4, 6, 8, 10, 12, 14, 16, 18, 20)
 
 
 def nvcc_path():

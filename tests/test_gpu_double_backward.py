@@ -27,6 +27,8 @@ def P():
 CASES = {
     "bcc-l8-s1": ("bcc", (3, 3, 3), 3.16, 0.1, 1, 1),
     "bcc-l16-s3": ("bcc", (3, 3, 2), 3.16, 0.1, 3, 2),
+    # config 3 recipe on a 2-cell, 32-atom FCC box (level 20, 4 species)
+    "fcc-l20-s4": ("fcc", (2, 2, 2), 3.6, 0.1, 4, 3),
 }
 
 
@@ -81,3 +83,30 @@ def test_hessian_vector_product_matches_finite_differences(P):
     got_t = tan["dtheta_tan"].cpu().numpy()
     assert np.abs(got_f - fd_f).max() <= 1e-5 * max(1.0, np.abs(fd_f).max())
     assert np.abs(got_t - fd_t).max() <= 1e-5 * max(1.0, np.abs(fd_t).max())
+
+
+@pytest.mark.slow
+def test_full_size_config3_directional_derivatives(P):
+    """256,000-atom FCC, level 20: the tangent of dE/dtheta and of the forces
+    along a random direction equals central differences of the FP64 results
+    (a property that holds at any size)."""
+    name = "fcc-l20-s4"
+    st = synth.crystal("fcc", (40, 40, 40), 3.6, 0.1, 4, 3)
+    pot = P.Potential.from_dict(pot_dict(name))
+    z = torch.tensor(st.z, device="cuda")
+    v = synth.rng(3, 10).normal(size=st.x.shape)
+    x = torch.tensor(st.x, device="cuda")
+    nl = P.mtp_build_neighbors(pot, x, st.cell, st.pbc)
+    tan = P.mtp_compute_efv_tangent(pot, nl, x, z, st.cell, torch.tensor(v, device="cuda"), precision=P.MTP_FP64)
+    # fourth-order central differences: close contacts make some Hessian
+    # entries ~1e7, where the second-order stencil's truncation error shows
+    h = 1e-5
+    vals = {}
+    for k in (-2, -1, 1, 2):
+        o = P.mtp_compute_efv(pot, nl, torch.tensor(st.x + k * h * v, device="cuda"), z, st.cell,
+                              precision=P.MTP_FP64, dtheta=True)
+        vals[k] = (o["dtheta"].cpu().numpy(), o["forces"].cpu().numpy())
+    fd_t = (-vals[2][0] + 8 * vals[1][0] - 8 * vals[-1][0] + vals[-2][0]) / (12 * h)
+    fd_f = (-vals[2][1] + 8 * vals[1][1] - 8 * vals[-1][1] + vals[-2][1]) / (12 * h)
+    assert np.abs(tan["dtheta_tan"].cpu().numpy() - fd_t).max() <= 1e-5 * np.abs(fd_t).max()
+    assert np.abs(tan["force_tan"].cpu().numpy() - fd_f).max() <= 1e-5 * np.abs(fd_f).max()

@@ -5,7 +5,13 @@ Tolerances (float64 outputs in every mode):
   FP64 path: site energies within 1e-12 relative (|dE_i| <= 1e-12 max(1, |E_i|)),
              total energy within 1e-12 of sum |E_i|, forces within 1e-10 eV/A,
              virial within 1e-10 of max |W| (and 1e-10 eV absolute);
-  mixed path: |dE_i| <= 1e-5 eV/atom and force RMS error <= 1e-4 eV/A.
+  mixed path: |dE_i| <= 1e-5 eV/atom and force RMS error <= 1e-4 eV/A (the
+             stated target of the level-16 workloads); for the level-20
+             workload, which states no mixed target, the bound derived from
+             FP32 rounding: |dE_i| <= 1e-5 eV + 1e-6 sum_alpha |xi_alpha B_alpha(i)|
+             (rounding 6e-8 times a cancellation allowance of ~16 on the sum of
+             basis contributions; level 20 has 446 basis functions with up to
+             ten moment factors).
 """
 import numpy as np
 import pytest
@@ -100,6 +106,8 @@ EFV_CASES = {
     "cfg2-bcc-l16-s3-rc5.6": ("bcc-l16-s3-rc5.6", ("bcc", (4, 4, 3), 3.16, 0.08, 3, 2)),
     "cfg5-bcc-l16-s1": ("bcc-l16-s1", ("bcc", (5, 4, 4), 3.16, 0.15, 1, 5)),
     "cfg4-gas-l16-s2": ("gas-l16-s2", ("gas", 45, 0, 0, 2, 4)),
+    # config 3 shape, reduced: level 20, four species, FCC, 54 neighbours
+    "cfg3-fcc-l20-s4": ("fcc-l20-s4", ("fcc", (2, 2, 2), 3.6, 0.1, 4, 3)),
 }
 
 _ORACLE_CACHE = {}
@@ -111,7 +119,9 @@ def oracle_efv(case):
         st = structure(*rec)
         model = oracle_model(name)
         nl = O.neighbor_list(st.x, st.cell, st.pbc, pot_dict(name)["r_cut"])
-        _ORACLE_CACHE[case] = (st, O.evaluate(model, st.x, st.z, st.cell, nl, want=("e", "f", "w", "dtheta")))
+        out = O.evaluate(model, st.x, st.z, st.cell, nl, want=("e", "f", "w", "dtheta"))
+        out["abs_terms"] = np.abs(O.basis_matrix(model, st.x, st.z, st.cell, nl)) @ np.abs(model.xi.numpy())
+        _ORACLE_CACHE[case] = (st, out)
     return _ORACLE_CACHE[case]
 
 
@@ -145,9 +155,10 @@ def test_efv_mixed_within_stated_error(P, case):
     name = EFV_CASES[case][0]
     st, ref = oracle_efv(case)
     got = run_gpu(P, name, st, P.MTP_MIXED, dtheta=True)
-    assert np.abs(got["e_atom"] - ref["e_atom"]).max() <= 1e-5
+    tol = 1e-5 + (1e-6 * ref["abs_terms"] if pot_dict(name)["level"] > 16 else 0.0)
+    assert np.all(np.abs(got["e_atom"] - ref["e_atom"]) <= tol)
     assert np.sqrt(np.mean((got["forces"] - ref["f"]) ** 2)) <= 1e-4
-    assert abs(got["e_total"][0] - ref["e"]) / st.n <= 1e-5
+    assert abs(got["e_total"][0] - ref["e"]) / st.n <= np.max(tol)
     assert np.abs(got["virial"] - ref["w"]).max() <= 1e-4 * max(1.0, np.abs(ref["w"]).max())
     theta_ref = np.concatenate([ref["dE_ds"], ref["dE_dc"].ravel(), ref["dE_dxi"]])
     assert np.abs(got["dtheta"] - theta_ref).max() <= 1e-4 * max(1.0, np.abs(theta_ref).max())
@@ -196,3 +207,23 @@ def test_full_size_config2_sampled_parity(P):
         assert np.abs(f[force_atoms] - ref["forces"]).max() <= f_tol * (1 if precision == P.MTP_FP64 else 10)
         assert np.abs(f.sum(axis=0)).max() <= (1e-8 if precision == P.MTP_FP64 else 1e-2)
         assert abs(out["e_total"].item() - e.sum()) <= 1e-9 * np.abs(e).sum()
+
+
+@pytest.mark.slow
+def test_full_size_config3_sampled_parity(P):
+    """256,000-atom FCC (40^3 cells, a = 3.6 A, sigma 0.1 A), 4 species, level 20:
+    sampled site energies and forces against the oracle (FP64)."""
+    name = "fcc-l20-s4"
+    st = synth.crystal("fcc", (40, 40, 40), 3.6, 0.1, 4, 3)
+    model = oracle_model(name)
+    centres = np.sort(synth.rng(3, 77).choice(st.n, 8, replace=False))
+    ref = oracle_sampled(model, st, 5.5, centres, centres[:2])
+    pot = gpu_pot(P, name)
+    x, z = dev(st)
+    nl = P.mtp_build_neighbors(pot, x, st.cell, st.pbc)
+    out = P.mtp_compute_efv(pot, nl, x, z, st.cell, precision=P.MTP_FP64)
+    e = out["e_atom"].cpu().numpy()
+    f = out["forces"].cpu().numpy()
+    assert np.all(np.abs(e[centres] - ref["e_atom"]) <= 1e-12 * np.maximum(1, np.abs(ref["e_atom"])))
+    assert np.abs(f[centres[:2]] - ref["forces"]).max() <= 1e-10
+    assert np.abs(f.sum(axis=0)).max() <= 1e-8
