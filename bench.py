@@ -237,6 +237,51 @@ def run_batch(P, torch, args):
             "outputs": "energies, forces, virials, dE/dtheta per configuration (mixed precision)"}
 
 
+def run_diff(P, torch, args):
+    """256,000-atom FCC (40^3 cells, a = 3.6 A, sigma 0.1 A), 4 species, level 20,
+    n_q 10, r_cut 5.5 A: forward (energy), backward (forces and dE/dtheta) and
+    double backward (directional derivative of dE/dtheta for a force-matching
+    loss), FP64 and mixed; mixed errors against FP64 are reported."""
+    import synth
+    st = synth.crystal("fcc", (40, 40, 40), 3.6, 0.1, 4, 3)
+    pot = P.Potential.from_file(os.path.join(ROOT, "potentials", "fcc-l20-s4.json"))
+    x = torch.tensor(st.x, device="cuda")
+    z = torch.tensor(st.z, device="cuda")
+    nl = P.mtp_build_neighbors(pot, x, st.cell, st.pbc)
+    v = torch.tensor(synth.target_forces(st.n, 3), device="cuda")
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+    def timed(fn, reps):
+        fn()
+        torch.cuda.synchronize()
+        e0.record()
+        for _ in range(reps):
+            r = fn()
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps, r
+
+    res = {"workload": "fcc-40x40x40 (256,000 atoms), level 20, 4 species, n_q 10, r_cut 5.5 A, sigma 0.1 A"}
+    outs = {}
+    for name, prec, reps in (("mixed", P.MTP_MIXED, 3), ("fp64", P.MTP_FP64, 1)):
+        ms_e, _ = timed(lambda: P.mtp_compute_efv(pot, nl, x, z, st.cell, precision=prec), reps)
+        ms_b, o = timed(lambda: P.mtp_compute_efv(pot, nl, x, z, st.cell, precision=prec, dtheta=True), reps)
+        ms_t, t = timed(lambda: P.mtp_compute_efv_tangent(pot, nl, x, z, st.cell, v, precision=prec), reps)
+        outs[name] = (o, t)
+        res[name] = {"efv_ms": ms_e, "efv_dtheta_ms": ms_b, "double_backward_ms": ms_t,
+                     "atom_steps_per_s": st.n / (ms_e * 1e-3)}
+    (om, tm), (od, td) = outs["mixed"], outs["fp64"]
+    import numpy as np
+    res["mixed_errors_vs_fp64"] = {
+        "e_atom_max_abs": float((om["e_atom"] - od["e_atom"]).abs().max()),
+        "force_rms": float(((om["forces"] - od["forces"]) ** 2).mean().sqrt()),
+        "dtheta_max_rel": float((om["dtheta"] - od["dtheta"]).abs().max() / od["dtheta"].abs().max()),
+        "dtheta_tan_max_rel": float((tm["dtheta_tan"] - td["dtheta_tan"]).abs().max()
+                                    / td["dtheta_tan"].abs().max())}
+    del np
+    return res
+
+
 def run_reference(args):
     rank, world = _dist()
     if rank != 0:
@@ -354,6 +399,7 @@ def run_ours(args):
 
     grade = None if args.no_grade else run_grade(P, torch, args)
     batch = None if args.no_batch else run_batch(P, torch, args)
+    diff = None if args.no_diff else run_diff(P, torch, args)
 
     hbm_gbs, max_mhz, peak_src = _peaks()
     flops_atom, fc = _flops_per_atom(pot.level, pot.n_q, pot.n_mu, nbar)
@@ -392,10 +438,11 @@ def run_ours(args):
                     "bytes_per_atom": bytes_atom, "peak_source": peak_src},
             "grade": grade,
             "batch": batch,
+            "differentiation": diff,
             "cpu_baseline": cpu,
             "e2e": ({"value": world * n_atoms / (e2e_ms * 1e-3), "unit": UNIT, "h2d_bytes_per_step": h2d,
                      "d2h_bytes_per_step": d2h} if e2e_ms else None),
-            "gpu_launches": 2 * args.steps,
+            "gpu_launches": 3 * args.steps,   # fixed-point pass, energy/force kernel, FP64 force conversion
             "clocks": clocks,
         }
         print(json.dumps(line))
@@ -406,7 +453,7 @@ def run_ours(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--cpu-sample", type=int, default=256)
@@ -415,6 +462,7 @@ def main():
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end steps")
     ap.add_argument("--no-grade", action="store_true", help="skip the extrapolation-grade workload")
     ap.add_argument("--no-batch", action="store_true", help="skip the 4096-configuration batch workload")
+    ap.add_argument("--no-diff", action="store_true", help="skip the level-20 differentiation workload")
     ap.add_argument("--cells", type=int, default=CELLS[0], help="BCC cells per edge (80: the 1,024,000-atom "
                     "workload; smaller values only for profiling captures)")
     args = ap.parse_args()

@@ -22,6 +22,8 @@ namespace mtp {
 
 struct NbrGeom {
   double cell[9];
+  float cellf[9];
+  float rc2_hi;       // prefilter bound: rc^2 plus the worst FP32 rounding of r^2
   double hinv[9];
   double origin[3];   // fractional origin of the bin grid (0 on periodic axes)
   double width[3];    // fractional width of one bin
@@ -44,11 +46,13 @@ static double unordered_bits(unsigned long long b) {
 }
 
 __global__ void wrap_kernel(const double* __restrict__ x, int64_t n, NbrGeom g, double* __restrict__ sw,
-                            int* __restrict__ wrapcnt, unsigned long long* __restrict__ extent) {
+                            int* __restrict__ wrapcnt, unsigned long long* __restrict__ extent,
+                            float4* __restrict__ xw) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   unsigned long long lo[3] = {~0ull, ~0ull, ~0ull}, hi[3] = {0ull, 0ull, 0ull};
   if (i < n) {
     const double px = x[3 * i], py = x[3 * i + 1], pz = x[3 * i + 2];
+    double sv[3];
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
       double s = px * g.hinv[0 + k] + py * g.hinv[3 + k] + pz * g.hinv[6 + k];
@@ -61,9 +65,14 @@ __global__ void wrap_kernel(const double* __restrict__ x, int64_t n, NbrGeom g, 
         if (s < 0.0) s = 0.0;
       }
       sw[3 * i + k] = s;
+      sv[k] = s;
       wrapcnt[3 * i + k] = w;
       lo[k] = hi[k] = ordered_bits(s);
     }
+    // wrapped Cartesian position in FP32, for the distance prefilter
+    xw[i] = make_float4((float)(sv[0] * g.cell[0] + sv[1] * g.cell[3] + sv[2] * g.cell[6]),
+                        (float)(sv[0] * g.cell[1] + sv[1] * g.cell[4] + sv[2] * g.cell[7]),
+                        (float)(sv[0] * g.cell[2] + sv[1] * g.cell[5] + sv[2] * g.cell[8]), 0.f);
   }
   // min/max of the fractional coordinates (used to lay bins over open axes)
 #pragma unroll
@@ -106,15 +115,20 @@ __global__ void bin_fill_kernel(const int* __restrict__ bin_of, int64_t n, const
 __device__ __forceinline__ int floor_div(int t, int m) { return t >= 0 ? t / m : -((-t + m - 1) / m); }
 
 // Visits every (j, n) within the cutoff of atom i; FILL writes them.
+// A candidate passes to the exact FP64 test only if its FP32 squared distance
+// (wrapped positions plus the bin wrap) is below rc2_hi, which exceeds R_cut^2
+// by more than the FP32 rounding can move it, so no pair within the cutoff is
+// dropped and the decision itself stays the exact FP64 expression.
 template <bool FILL>
 __global__ void pair_kernel(const double* __restrict__ x, const double* __restrict__ sw, const int* __restrict__ wrapcnt,
-                            int64_t n, NbrGeom g, const int* __restrict__ bin_start, const int* __restrict__ bin_count,
-                            const int* __restrict__ bin_atoms, int* __restrict__ counts,
-                            const int64_t* __restrict__ offsets, int32_t* __restrict__ out_j,
+                            const float4* __restrict__ xw, int64_t n, NbrGeom g, const int* __restrict__ bin_start,
+                            const int* __restrict__ bin_count, const int* __restrict__ bin_atoms,
+                            int* __restrict__ counts, const int64_t* __restrict__ offsets, int32_t* __restrict__ out_j,
                             int32_t* __restrict__ out_img, int* __restrict__ status) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   const double xi = x[3 * i], yi = x[3 * i + 1], zi = x[3 * i + 2];
+  const float4 pw = xw[i];
   const int wi[3] = {wrapcnt[3 * i], wrapcnt[3 * i + 1], wrapcnt[3 * i + 2]};
   const int bi[3] = {bin_coord(sw[3 * i], g, 0), bin_coord(sw[3 * i + 1], g, 1), bin_coord(sw[3 * i + 2], g, 2)};
   int found = 0;
@@ -133,8 +147,15 @@ __global__ void pair_kernel(const double* __restrict__ x, const double* __restri
         else if (t2 < 0 || t2 >= g.nb[2]) continue;
         const int b = (c0 * g.nb[1] + c1) * g.nb[2] + c2;
         const int s0 = bin_start[b], cnt = bin_count[b];
+        const float fq0 = (float)q0, fq1 = (float)q1, fq2 = (float)q2;
+        const float shx = fq0 * g.cellf[0] + fq1 * g.cellf[3] + fq2 * g.cellf[6] - pw.x;
+        const float shy = fq0 * g.cellf[1] + fq1 * g.cellf[4] + fq2 * g.cellf[7] - pw.y;
+        const float shz = fq0 * g.cellf[2] + fq1 * g.cellf[5] + fq2 * g.cellf[8] - pw.z;
         for (int u = 0; u < cnt; ++u) {
           const int j = bin_atoms[s0 + u];
+          const float4 qw = xw[j];
+          const float fx = qw.x + shx, fy = qw.y + shy, fz = qw.z + shz;
+          if (fx * fx + fy * fy + fz * fz >= g.rc2_hi) continue;
           // image of j relative to the unwrapped positions
           const int n1 = q0 + wi[0] - wrapcnt[3 * j];
           const int n2 = q1 + wi[1] - wrapcnt[3 * j + 1];
@@ -228,6 +249,8 @@ int build_neighbors(mtp_nlist* nl, const double* x, int64_t n, const double* cel
     g.pbc[k] = pbc[k] ? 1 : 0;
   }
   g.rc2 = r_cut * r_cut;
+  for (int k = 0; k < 9; ++k) g.cellf[k] = (float)cell[k];
+
   for (int k = 0; k < 9; ++k) nl->cell[k] = cell[k];
   for (int k = 0; k < 3; ++k) nl->pbc[k] = g.pbc[k];
   nl->r_cut = r_cut;
@@ -236,11 +259,12 @@ int build_neighbors(mtp_nlist* nl, const double* x, int64_t n, const double* cel
   const int T = 256;
   const unsigned blocks = (unsigned)((n + T - 1) / T);
   int rc;
-  if ((rc = nl->wrapped.ensure(sizeof(double) * 3 * std::max<int64_t>(n, 1) + sizeof(int) * 3 * std::max<int64_t>(n, 1) +
-                                64)) != MTP_OK)
+  const int64_t n1 = std::max<int64_t>(n, 1);
+  if ((rc = nl->wrapped.ensure(sizeof(float4) * n1 + sizeof(double) * 3 * n1 + sizeof(int) * 3 * n1 + 64)) != MTP_OK)
     return rc;
-  double* sw = nl->wrapped.as<double>();
-  int* wrapcnt = reinterpret_cast<int*>(sw + 3 * std::max<int64_t>(n, 1));
+  float4* xw = nl->wrapped.as<float4>();
+  double* sw = reinterpret_cast<double*>(xw + n1);
+  int* wrapcnt = reinterpret_cast<int*>(sw + 3 * n1);
   unsigned long long* extent = reinterpret_cast<unsigned long long*>(
       (reinterpret_cast<uintptr_t>(wrapcnt + 3 * std::max<int64_t>(n, 1)) + 15) & ~uintptr_t(15));
   if ((rc = nl->status.ensure(sizeof(int) * 4)) != MTP_OK) return rc;
@@ -248,10 +272,10 @@ int build_neighbors(mtp_nlist* nl, const double* x, int64_t n, const double* cel
   MTP_TRY_CUDA(cudaMemsetAsync(status, 0, sizeof(int), stream));
   const unsigned long long ext_init[6] = {~0ull, 0ull, ~0ull, 0ull, ~0ull, 0ull};
   MTP_TRY_CUDA(cudaMemcpyAsync(extent, ext_init, sizeof(ext_init), cudaMemcpyHostToDevice, stream));
-  if (n > 0) wrap_kernel<<<blocks, T, 0, stream>>>(x, n, g, sw, wrapcnt, extent);
+  if (n > 0) wrap_kernel<<<blocks, T, 0, stream>>>(x, n, g, sw, wrapcnt, extent, xw);
   MTP_TRY_CUDA(cudaGetLastError());
-  unsigned long long ext[6];
-  MTP_TRY_CUDA(cudaMemcpyAsync(ext, extent, sizeof(ext), cudaMemcpyDeviceToHost, stream));
+  unsigned long long ext_bits[6];
+  MTP_TRY_CUDA(cudaMemcpyAsync(ext_bits, extent, sizeof(ext_bits), cudaMemcpyDeviceToHost, stream));
   MTP_TRY_CUDA(cudaStreamSynchronize(stream));
   int64_t nbins = 1;
   for (int k = 0; k < 3; ++k) {
@@ -263,8 +287,8 @@ int build_neighbors(mtp_nlist* nl, const double* x, int64_t n, const double* cel
     } else {
       double lo = 0.0, hi = 0.0;
       if (n > 0) {
-        lo = unordered_bits(ext[2 * k]);
-        hi = unordered_bits(ext[2 * k + 1]);
+        lo = unordered_bits(ext_bits[2 * k]);
+        hi = unordered_bits(ext_bits[2 * k + 1]);
       }
       const double w = r_cut / h[k];   // fractional width of one cutoff
       g.origin[k] = lo;
@@ -276,6 +300,26 @@ int build_neighbors(mtp_nlist* nl, const double* x, int64_t n, const double* cel
     g.reach[k] = (int)std::floor(r_cut * g.nb[k] / h[k] * (g.pbc[k] ? 1.0 : 0.0)) + 1;
     if (!g.pbc[k]) g.reach[k] = std::max(1, (int)std::ceil(r_cut / (g.width[k] * h[k])));
     nbins *= g.nb[k];
+  }
+  {
+    // FP32 prefilter margin.  Along cell vector k the wrapped fractional
+    // coordinate lies in [lo_k, hi_k] ([0, 1) on periodic axes) and the bin
+    // wrap q_k is at most (reach_k + nb_k) / nb_k + 1 in magnitude, so every
+    // position, shift and pair vector is below ext = sum_k |h_k| (span_k + q_k)
+    // in size and each of the few FP32 roundings on the way is below
+    // ext 2^-24 per component.
+    double ext = 0.0;
+    for (int k = 0; k < 3; ++k) {
+      const double len = std::sqrt(cell[3 * k] * cell[3 * k] + cell[3 * k + 1] * cell[3 * k + 1] +
+                                   cell[3 * k + 2] * cell[3 * k + 2]);
+      double span = 1.0;
+      if (!g.pbc[k] && n > 0)
+        span = std::max(std::fabs(unordered_bits(ext_bits[2 * k])), std::fabs(unordered_bits(ext_bits[2 * k + 1])));
+      const double qmax = g.pbc[k] ? (double)(g.reach[k] + g.nb[k]) / g.nb[k] + 1.0 : 0.0;
+      ext += len * (span + qmax + 1.0);
+    }
+    const double err = 8.0 * ext * std::ldexp(1.0, -24) * std::sqrt(3.0);
+    g.rc2_hi = (float)((r_cut + 2.0 * err) * (r_cut + 2.0 * err) * (1.0 + 1e-5));
   }
   if ((rc = nl->bins.ensure(sizeof(int) * (2 * nbins + 1))) != MTP_OK) return rc;
   int* bin_count = nl->bins.as<int>();
@@ -304,7 +348,7 @@ int build_neighbors(mtp_nlist* nl, const double* x, int64_t n, const double* cel
   if (n > 0) bin_fill_kernel<<<blocks, T, 0, stream>>>(bin_of, n, bin_start, cursor, bin_atoms);
   MTP_TRY_CUDA(cudaGetLastError());
   if (n > 0)
-    pair_kernel<false><<<blocks, T, 0, stream>>>(x, sw, wrapcnt, n, g, bin_start, bin_count, bin_atoms, counts, nullptr,
+    pair_kernel<false><<<blocks, T, 0, stream>>>(x, sw, wrapcnt, xw, n, g, bin_start, bin_count, bin_atoms, counts, nullptr,
                                                  nullptr, nullptr, status);
   MTP_TRY_CUDA(cudaGetLastError());
   if ((rc = nl->offsets.ensure(sizeof(int64_t) * (n + 1))) != MTP_OK) return rc;
@@ -325,7 +369,7 @@ int build_neighbors(mtp_nlist* nl, const double* x, int64_t n, const double* cel
   if ((rc = nl->nbr_j.ensure(sizeof(int32_t) * std::max<int64_t>(total, 1))) != MTP_OK) return rc;
   if ((rc = nl->nbr_img.ensure(sizeof(int32_t) * std::max<int64_t>(total, 1))) != MTP_OK) return rc;
   if (n > 0)
-    pair_kernel<true><<<blocks, T, 0, stream>>>(x, sw, wrapcnt, n, g, bin_start, bin_count, bin_atoms, nullptr, offsets,
+    pair_kernel<true><<<blocks, T, 0, stream>>>(x, sw, wrapcnt, xw, n, g, bin_start, bin_count, bin_atoms, nullptr, offsets,
                                                 nl->nbr_j.as<int32_t>(), nl->nbr_img.as<int32_t>(), status);
   MTP_TRY_CUDA(cudaGetLastError());
   return MTP_OK;
