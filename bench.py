@@ -29,6 +29,10 @@ POTENTIAL = "bcc-l16-s3"
 CELLS = (80, 80, 80)
 SM_COUNT = 152
 FP32_LANES = 128
+# DRAM read + write per atom of efv_kernel<MtpLevel16, float, 0> from the ncu
+# capture in profiles/efv_kernel_bcc70_l16_mixed.md (686,000 atoms; traffic
+# scales with the atom count).  Set to None whenever that kernel changes.
+EFV_TRAFFIC_BYTES_PER_ATOM = (184.4928e6 + 139.284224e6) / 686000
 
 
 def _peaks():
@@ -431,7 +435,9 @@ def run_ours(args):
             "mixed_over_fp64": (ms64 / ms) if ms64 else None,
             "nbr_build_ms": nbr_ms,
             "roofline": {"bound": "alu", "achieved": achieved_tflops, "peak": peak_tflops, "unit": "TFLOP/s",
-                         "frac": achieved_tflops / peak_tflops, "traffic": None,
+                         "frac": achieved_tflops / peak_tflops,
+                         "traffic": (EFV_TRAFFIC_BYTES_PER_ATOM * n_atoms
+                                     if EFV_TRAFFIC_BYTES_PER_ATOM and args.cells == CELLS[0] else None),
                          "peak_source": "152 SMs x 128 FP32 lanes x 2 flop x %.0f MHz (max SM clock)" % mhz,
                          "flops_per_atom": flops_atom},
             "hbm": {"achieved": hbm_achieved, "peak": hbm_gbs, "unit": "GB/s", "frac": hbm_achieved / hbm_gbs,
