@@ -156,22 +156,34 @@ def run_grade(P, torch, args):
     a_inv = torch.tensor(act["a_inv"], dtype=torch.float64, device="cuda").reshape(m, m)
     a_cfg = torch.tensor(act["a_inv_cfg"], dtype=torch.float64, device="cuda").reshape(m, m)
     nl = P.mtp_build_neighbors(pot, x, st.cell, st.pbc)
-    out = P.mtp_compute_grade(pot, nl, x, z, st.cell, a_inv=a_inv, a_inv_cfg=a_cfg)
-    torch.cuda.synchronize()
-    steps = 3
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    e0.record()
-    for _ in range(steps):
-        out = P.mtp_compute_grade(pot, nl, x, z, st.cell, a_inv=a_inv, a_inv_cfg=a_cfg, out=out)
-    e1.record()
-    torch.cuda.synchronize()
-    ms = e0.elapsed_time(e1) / steps
-    flags = out["flags"].cpu().numpy()
-    return {"workload": "bcc-50x50x100 (500,000 atoms), level 16, 1 species, sigma 0.15 A; active sets by MaxVol",
-            "value": st.n / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms, "precision": "fp64",
-            "gamma_max": out["gamma_max"], "gamma_cfg": out["gamma_cfg"], "n_ambiguous": out["n_ambiguous"],
-            "n_selected": int((flags & 1).sum()), "n_break": int((flags & 2).sum() // 2)}
+    res = {"workload": "bcc-50x50x100 (500,000 atoms), level 16, 1 species, sigma 0.15 A; active sets by MaxVol",
+           "unit": UNIT}
+    flops_fp64 = 2.0 * st.n * m * m
+    for name, method in (("tensor", P.MTP_GRADE_TENSOR), ("fp64", P.MTP_GRADE_FP64)):
+        out = P.mtp_compute_grade(pot, nl, x, z, st.cell, a_inv=a_inv, a_inv_cfg=a_cfg, method=method)
+        torch.cuda.synchronize()
+        steps = 3
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(steps):
+            out = P.mtp_compute_grade(pot, nl, x, z, st.cell, a_inv=a_inv, a_inv_cfg=a_cfg, method=method, out=out)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / steps
+        flags = out["flags"].cpu().numpy()
+        res[name] = {"value": st.n / (ms * 1e-3), "ms_per_step": ms, "gamma_max": out["gamma_max"],
+                     "gamma_cfg": out["gamma_cfg"], "n_ambiguous": out["n_ambiguous"],
+                     "n_rechecked": out["n_rechecked"], "n_selected": int((flags & 1).sum()),
+                     "n_break": int((flags & 2).sum() // 2)}
+        if name == "tensor":
+            res["flags_tensor"] = flags
+    res["flags_identical"] = bool((res.pop("flags_tensor") == flags).all())
+    res["value"] = res["tensor"]["value"]
+    res["ms_per_step"] = res["tensor"]["ms_per_step"]
+    res["product_flops_fp64_equivalent"] = flops_fp64
+    res["mma_flops_executed"] = 2.0 * 28 * 128 * 128 * 128 * ((st.n + 127) // 128)
+    return res
 
 
 def run_batch(P, torch, args):

@@ -150,17 +150,47 @@ int mtp_compute_efv_tangent(mtp_handle* h, const mtp_nlist* nl, const double* x_
  *     gamma_i > tau_sel, bit 1 = gamma_i > tau_brk;
  *   configuration mode: gamma_cfg = max_k |((sum_i b_i) A_cfg^-1)_k|.
  * a_inv_dev / a_inv_cfg_dev: DEVICE, m x m row-major FP64 inverses of the
- * active sets (either may be NULL, not both).  Basis rows and products are
- * FP64 throughout; chunk_atoms bounds the FP64 row scratch (0 = 262144).
+ * active sets (either may be NULL, not both).  Basis rows are FP64;
+ * chunk_atoms bounds the row scratch (0 = 262144).
+ * method (neighbourhood mode):
+ *   MTP_GRADE_TENSOR: the product on the BF16 tensor cores (tcgen05) by
+ *     error-free splitting of both FP64 operands into 7 BF16 slices each
+ *     (exact FP32 accumulation of every slice group), grade error at most
+ *     2^-47 max|b_i D| max|D^-1 A^-1| + 2^-52 gamma_i for a power-of-two
+ *     column balancing D; rows within max(5% of a threshold, that bound) of
+ *     either threshold are re-checked in FP64 and take the FP64 grade and
+ *     flags.  Needs m <= 128 (MTP_ERR_UNSUPPORTED otherwise).
+ *   MTP_GRADE_FP64: every product in FP64 on the CUDA cores.
  * Outputs: gamma_dev [N] FP64 and flags_dev [N] uint8 (DEVICE, neighbourhood
- * mode); gamma_max, gamma_cfg, n_ambiguous on the HOST (nullable):
- * n_ambiguous counts grades within their FP64 error bound of a threshold.
+ * mode); gamma_max, gamma_cfg, n_ambiguous, n_rechecked on the HOST
+ * (nullable): n_ambiguous counts FP64 grades within their FP64 error bound of
+ * a threshold, n_rechecked the rows the tensor-core method sent to FP64.
  * Synchronises `stream`.  Returns MTP_STATUS_BREAK when the largest grade
- * exceeds tau_brk, MTP_OK otherwise, or an error code. */
+ * exceeds tau_brk, MTP_OK otherwise, or an error code (MTP_ERR_TIMEOUT if a
+ * device-side wait of the tensor-core kernel gave up). */
+typedef enum { MTP_GRADE_TENSOR = 0, MTP_GRADE_FP64 = 1 } mtp_grade_method;
 int mtp_compute_grade(mtp_handle* h, const mtp_nlist* nl, const double* x_dev, const int32_t* z_dev,
                       int64_t n_atoms, const double* cell, const double* a_inv_dev, const double* a_inv_cfg_dev,
-                      double tau_sel, double tau_brk, int64_t chunk_atoms, double* gamma_dev, uint8_t* flags_dev,
-                      double* gamma_max, double* gamma_cfg, int64_t* n_ambiguous, void* stream);
+                      double tau_sel, double tau_brk, int64_t chunk_atoms, int32_t method, double* gamma_dev,
+                      uint8_t* flags_dev, double* gamma_max, double* gamma_cfg, int64_t* n_ambiguous,
+                      int64_t* n_rechecked, void* stream);
+
+/* Verification hook for the tensor-core grade product (same kernel as
+ * MTP_GRADE_TENSOR; the paper has no counterpart, it exists so that tests can
+ * check the tensor-core arithmetic bit for bit).  Inputs, all DEVICE:
+ *   xs_dev: BF16 bit patterns, [ceil(n_rows/128)][7][128 x 128] X slices in
+ *     the kernel's operand layout: element (row i, column j) of a tile at
+ *     (j/8)*1024 + (i/8)*64 + (i%8)*8 + j%8;
+ *   ys_dev: [2][7][64 x 128] Y slices, element (column k, row j) of a half
+ *     at (j/8)*512 + (k/8)*64 + (k%8)*8 + j%8;
+ *   fexp_dev [128] column exponents, erow_dev [n_rows] row exponents.
+ * Outputs (DEVICE): acc_dev (nullable) [n_rows][2][7][64] FP32 slice-group
+ * sums G_d = sum_{s+t=d} X_s Y_t for d = 2..8 per column half;
+ * gamma_bits_dev [n_rows] the FP64 bit patterns of the grades.
+ * Synchronises `stream`. */
+int mtp_grade_tc_selftest(const uint16_t* xs_dev, const uint16_t* ys_dev, const int32_t* fexp_dev,
+                          const int32_t* erow_dev, int64_t n_rows, float* acc_dev, uint64_t* gamma_bits_dev,
+                          void* stream);
 
 /* Batches of many small periodic configurations (SURVEY workload: thousands
  * of 8..256-atom cells), evaluated in one persistent launch.

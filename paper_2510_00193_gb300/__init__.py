@@ -14,12 +14,12 @@ import json
 import numpy as np
 
 from . import _lib
-from ._lib import MTP_FP64, MTP_MIXED, MtpError, check
+from ._lib import MTP_FP64, MTP_GRADE_FP64, MTP_GRADE_TENSOR, MTP_MIXED, MtpError, check
 
 __all__ = [
-    "MTP_FP64", "MTP_MIXED", "MtpError", "Potential", "NeighborList", "mtp_basis_info", "mtp_basis_table",
+    "MTP_FP64", "MTP_MIXED", "MTP_GRADE_TENSOR", "MTP_GRADE_FP64", "MtpError", "Potential", "NeighborList", "mtp_basis_info", "mtp_basis_table",
     "mtp_load_params", "mtp_build_neighbors", "mtp_compute_efv", "mtp_compute_efv_noalloc", "mtp_compute_grade",
-    "mtp_device_status", "mtp_compute_efv_tangent", "Batch", "mtp_batch_create", "mtp_compute_batch", "mtp_batch_tune",
+    "mtp_grade_tc_selftest", "mtp_device_status", "mtp_compute_efv_tangent", "Batch", "mtp_batch_create", "mtp_compute_batch", "mtp_batch_tune",
     "library_path",
 ]
 
@@ -250,33 +250,53 @@ def mtp_compute_efv_noalloc(potential: Potential, nlist: NeighborList, x, z, cel
 
 
 def mtp_compute_grade(potential: Potential, nlist: NeighborList, x, z, cell, a_inv=None, a_inv_cfg=None,
-                      tau_sel=2.0, tau_brk=10.0, chunk_atoms=0, out=None, stream=None) -> dict:
+                      tau_sel=2.0, tau_brk=10.0, chunk_atoms=0, method=None, out=None, stream=None) -> dict:
     """Extrapolation grades.  a_inv / a_inv_cfg: [m, m] float64 CUDA tensors
-    (inverse active sets for neighbourhood / configuration mode).  Returns
-    gamma [N] float64 and flags [N] uint8 (CUDA tensors, neighbourhood mode),
-    gamma_max, gamma_cfg, n_ambiguous and status (1 = above the break
+    (inverse active sets for neighbourhood / configuration mode).  method:
+    MTP_GRADE_TENSOR (default; tensor cores with error-free slicing and an
+    FP64 re-check near the thresholds) or MTP_GRADE_FP64.  Returns gamma [N]
+    float64 and flags [N] uint8 (CUDA tensors, neighbourhood mode), gamma_max,
+    gamma_cfg, n_ambiguous, n_rechecked and status (1 = above the break
     threshold)."""
     import torch
     n = x.shape[0]
     m = potential.m
     dev = x.device
+    if method is None:
+        method = MTP_GRADE_TENSOR
     if out is None:
         out = {"gamma": torch.empty(n, dtype=torch.float64, device=dev) if a_inv is not None else None,
                "flags": torch.empty(n, dtype=torch.uint8, device=dev) if a_inv is not None else None}
     c = _host_d(cell, 9)
     gmax, gcfg = ctypes.c_double(), ctypes.c_double()
-    amb = ctypes.c_int64()
+    amb, rchk = ctypes.c_int64(), ctypes.c_int64()
     rc = check(_lib.load().mtp_compute_grade(
         potential.handle, nlist.handle, _dptr(x, torch.float64, 3 * n, "x"), _dptr(z, torch.int32, n, "z"), n,
         c.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
         _dptr(a_inv, torch.float64, m * m, "a_inv") if a_inv is not None else None,
         _dptr(a_inv_cfg, torch.float64, m * m, "a_inv_cfg") if a_inv_cfg is not None else None,
-        float(tau_sel), float(tau_brk), int(chunk_atoms),
+        float(tau_sel), float(tau_brk), int(chunk_atoms), int(method),
         _dptr(out["gamma"], torch.float64, n, "gamma") if a_inv is not None else None,
         _dptr(out["flags"], torch.uint8, n, "flags") if a_inv is not None else None,
-        ctypes.byref(gmax), ctypes.byref(gcfg), ctypes.byref(amb), _stream_ptr(stream)))
-    out.update(gamma_max=gmax.value, gamma_cfg=gcfg.value, n_ambiguous=amb.value, status=rc)
+        ctypes.byref(gmax), ctypes.byref(gcfg), ctypes.byref(amb), ctypes.byref(rchk), _stream_ptr(stream)))
+    out.update(gamma_max=gmax.value, gamma_cfg=gcfg.value, n_ambiguous=amb.value, n_rechecked=rchk.value, status=rc)
     return out
+
+
+def mtp_grade_tc_selftest(xs, ys, fexp, erow, n_rows, acc=None, stream=None):
+    """Runs the tensor-core grade product on caller-made slices (verification
+    hook; layouts as in mtp.h).  xs, ys: int16 CUDA tensors of BF16 bit
+    patterns; fexp [128], erow [n_rows]: int32 CUDA tensors; acc: optional
+    float32 CUDA tensor [n_rows, 2, 7, 64].  Returns the grades as float64."""
+    import torch
+    gbits = torch.zeros(n_rows, dtype=torch.int64, device=xs.device)
+    tiles = (n_rows + 127) // 128
+    check(_lib.load().mtp_grade_tc_selftest(
+        _dptr(xs, torch.int16, tiles * 7 * 128 * 128, "xs"), _dptr(ys, torch.int16, 2 * 7 * 64 * 128, "ys"),
+        _dptr(fexp, torch.int32, 128, "fexp"), _dptr(erow, torch.int32, n_rows, "erow"), int(n_rows),
+        _dptr(acc, torch.float32, n_rows * 2 * 7 * 64, "acc") if acc is not None else None,
+        _dptr(gbits, torch.int64, n_rows, "gamma_bits"), _stream_ptr(stream)))
+    return gbits.view(torch.float64)
 
 
 class Batch:

@@ -18,6 +18,8 @@ STATUS_NAMES = {
 }
 MTP_FP64 = 0
 MTP_MIXED = 1
+MTP_GRADE_TENSOR = 0
+MTP_GRADE_FP64 = 1
 
 
 class MtpError(RuntimeError):
@@ -61,7 +63,8 @@ SIGNATURES = {
     "mtp_compute_efv": (ctypes.c_int, [_VP, _VP, _VP, _VP, _I64, _P_D, _I32, _I64, _VP, _VP, _VP, _VP, _VP, _VP]),
     "mtp_compute_efv_tangent": (ctypes.c_int, [_VP, _VP, _VP, _VP, _I64, _P_D, _I32, _VP, _VP, _VP, _VP]),
     "mtp_compute_grade": (ctypes.c_int, [_VP, _VP, _VP, _VP, _I64, _P_D, _VP, _VP, ctypes.c_double, ctypes.c_double,
-                                         _I64, _VP, _VP, _P_D, _P_D, _P_I64, _VP]),
+                                         _I64, _I32, _VP, _VP, _P_D, _P_D, _P_I64, _P_I64, _VP]),
+    "mtp_grade_tc_selftest": (ctypes.c_int, [_VP, _VP, _VP, _VP, _I64, _VP, _VP, _VP]),
     "mtp_batch_create": (ctypes.c_int, [_VP, _I32, _P_I64, _P_D, _P_I32, _VP, _I32, ctypes.POINTER(_VP), _VP]),
     "mtp_batch_nlist": (ctypes.c_int, [_VP, ctypes.POINTER(_VP)]),
     "mtp_compute_batch": (ctypes.c_int, [_VP, _VP, _VP, _VP, _I32, _VP, _VP, _VP, _VP, _VP, _VP]),

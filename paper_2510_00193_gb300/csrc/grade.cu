@@ -2,18 +2,24 @@
 // gamma_cfg = max_k |((sum_i b_i) A_cfg^-1)_k| (configuration mode), with the
 // selection and break thresholds of paper Sec. 2.1 / Sec. 2.3.
 //
-// Precision.  Everything is FP64.  On active sets drawn from near-perfect
-// lattices the product b_i A^-1 cancels by a factor sum_j |b_ij A_jk| / gamma_i
-// of about 5e7 (median over a sigma = 0.15 A BCC box against a sigma = 0.05 A
-// pool), so neither FP32 basis values nor a TF32/BF16 product can decide a
-// flag; FP64 leaves a relative error of about 1e-8.  Each row carries the bound
-// eps_i = kGradeRelErr * sum_j |b_ij| max_k |A_jk|; a row whose grade lies
-// within eps_i of a threshold is counted as ambiguous (its flag is still the
-// FP64 comparison).
+// Basis rows are FP64: on active sets drawn from near-perfect lattices the
+// product b_i A^-1 cancels by a factor sum_j |b_ij A_jk| / gamma_i of about
+// 5e7 (median over a sigma = 0.15 A BCC box against a sigma = 0.05 A pool),
+// so FP32 basis values cannot decide a flag.
+//
+// Two methods for the neighbourhood-mode product:
+//   MTP_GRADE_TENSOR (default): the BF16 tensor cores with error-free slicing
+//     (grade_tc.cu); rows within max(5% of a threshold, the slicing bound) of
+//     a threshold are re-checked by the FP64 kernel below on a compacted list.
+//   MTP_GRADE_FP64: every row through the FP64 kernel below.
+// In both, each FP64 result carries the bound eps_i = kGradeRelErr *
+// sum_j |b_ij| max_k |A_jk|; a row whose FP64 grade lies within eps_i of a
+// threshold is counted as ambiguous (its flag is still the FP64 comparison).
 //
 // gemm_grade_kernel: 64 rows x all m columns per block of 256 threads, K in
 // blocks of 16 staged in shared memory, 4 x 8 FP64 accumulators per thread,
-// fused row maximum, bound, flags and the running maximum grade.
+// fused row maximum, bound, flags and the running maximum grade; rows come
+// either contiguously or from an index list.
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -32,13 +38,19 @@ __global__ void __launch_bounds__(256) gemm_grade_kernel(const double* __restric
                                                          double tau_brk, double* __restrict__ gamma,
                                                          uint8_t* __restrict__ flags,
                                                          unsigned long long* __restrict__ gmax_bits,
-                                                         unsigned long long* __restrict__ n_ambiguous) {
+                                                         unsigned long long* __restrict__ n_ambiguous,
+                                                         const int32_t* __restrict__ list,
+                                                         const unsigned* __restrict__ list_n) {
   __shared__ double As[kGemmBK][kGemmBM + 1];
   __shared__ double Bs[kGemmBK][kGemmBN];
   __shared__ double red[kGemmBM][17];
   const int tid = threadIdx.x;
   const int ty = tid / 16, tx = tid % 16;
   const int64_t row0 = (int64_t)blockIdx.x * kGemmBM;
+  if (list) {
+    n = (int64_t)*list_n;   // rows are list[0 .. *list_n)
+    if (row0 >= n) return;  // uniform over the block
+  }
   double acc[4][8];
 #pragma unroll
   for (int r = 0; r < 4; ++r)
@@ -50,7 +62,8 @@ __global__ void __launch_bounds__(256) gemm_grade_kernel(const double* __restric
       const int e = tid + 256 * t;
       const int rr = e / kGemmBK, kk = e % kGemmBK;
       const int64_t gr = row0 + rr;
-      As[kk][rr] = (gr < n && kb + kk < m) ? rows[gr * m + kb + kk] : 0.0;
+      const int64_t src = (gr < n && list) ? (int64_t)list[gr] : gr;
+      As[kk][rr] = (gr < n && kb + kk < m) ? rows[src * m + kb + kk] : 0.0;
     }
 #pragma unroll
     for (int t = 0; t < (kGemmBK * kGemmBN) / 256; ++t) {
@@ -82,8 +95,9 @@ __global__ void __launch_bounds__(256) gemm_grade_kernel(const double* __restric
   }
   __syncthreads();
   if (tid < kGemmBM) {
-    const int64_t gr = row0 + tid;
+    int64_t gr = row0 + tid;
     if (gr < n) {
+      if (list) gr = list[gr];
       double g = 0.0;
       for (int t = 0; t < 16; ++t) g = fmax(g, red[tid][t]);
       double bound = 0.0;
@@ -136,14 +150,24 @@ __global__ void cfg_grade_kernel(const double* __restrict__ bsum, const double* 
   }
 }
 
+// total += *count (one thread).
+__global__ void add_count_kernel(unsigned long long* total, const unsigned* count) { *total += *count; }
+
 }  // namespace mtp
 
 using namespace mtp;
 
+namespace {
+
+size_t align256(size_t v) { return (v + 255) & ~size_t(255); }
+
+}  // namespace
+
 extern "C" int mtp_compute_grade(mtp_handle* h, const mtp_nlist* nl, const double* x, const int32_t* z, int64_t n,
                                  const double* cell, const double* a_inv, const double* a_inv_cfg, double tau_sel,
-                                 double tau_brk, int64_t chunk_atoms, double* gamma, uint8_t* flags,
-                                 double* gamma_max, double* gamma_cfg, int64_t* n_ambiguous, void* stream) {
+                                 double tau_brk, int64_t chunk_atoms, int32_t method, double* gamma, uint8_t* flags,
+                                 double* gamma_max, double* gamma_cfg, int64_t* n_ambiguous, int64_t* n_rechecked,
+                                 void* stream) {
   if (!h || !nl || !cell || (n > 0 && (!x || !z))) {
     set_error("mtp_compute_grade: NULL argument");
     return MTP_ERR_ARG;
@@ -168,22 +192,59 @@ extern "C" int mtp_compute_grade(mtp_handle* h, const mtp_nlist* nl, const doubl
     set_error("mtp_compute_grade: chunk_atoms < 0");
     return MTP_ERR_ARG;
   }
+  if (method != MTP_GRADE_TENSOR && method != MTP_GRADE_FP64) {
+    set_error("mtp_compute_grade: unknown method %d", (int)method);
+    return MTP_ERR_ARG;
+  }
   if (!h->ops->rows) {
     set_error("mtp_compute_grade: level %d has no basis-row kernel", h->level);
     return MTP_ERR_UNSUPPORTED;
   }
   cudaStream_t s = (cudaStream_t)stream;
   const int m = h->m;
+  const bool tensor = a_inv && method == MTP_GRADE_TENSOR;
+  if (tensor && m > kTcMaxBasis) {
+    set_error("mtp_compute_grade: the tensor-core method supports m <= %d (m = %d); use MTP_GRADE_FP64", kTcMaxBasis,
+              m);
+    return MTP_ERR_UNSUPPORTED;
+  }
   const int64_t chunk = chunk_atoms > 0 ? std::min<int64_t>(chunk_atoms, std::max<int64_t>(n, 1))
                                         : std::min<int64_t>(std::max<int64_t>(n, 1), 262144);
   int rc;
-  // scratch: [gmax bits, ambiguous count, cfg(2)] | amax [m] | bsum [m] | rows [chunk][m]
+  // scratch: head [gmax bits, ambiguous count, cfg(2), rechecked, list count, status] | amax [m] | bsum [m] |
+  //          rows [chunk][m] | tensor-core method: colmax, dexp, fexp, fmax, Y slices, erow, gamma bits, list, X slices
   const size_t head = 8;
-  if ((rc = h->grade.ensure(sizeof(double) * (head + 2 * (size_t)m + (size_t)chunk * m))) != MTP_OK) return rc;
+  size_t off = sizeof(double) * (head + 2 * (size_t)m + (size_t)chunk * m);
+  size_t o_colmax = 0, o_dexp = 0, o_fexp = 0, o_fmax = 0, o_ys = 0, o_erow = 0, o_gbits = 0, o_list = 0, o_xs = 0;
+  if (tensor) {
+    o_colmax = off = align256(off);
+    off += sizeof(unsigned long long) * kTcMaxBasis;
+    o_dexp = off = align256(off);
+    off += sizeof(int) * kTcMaxBasis;
+    o_fexp = off = align256(off);
+    off += sizeof(int) * kTcMaxBasis;
+    o_fmax = off = align256(off);
+    off += sizeof(int) * 4;
+    o_ys = off = align256(off);
+    off += tc_y_bytes();
+    o_erow = off = align256(off);
+    off += sizeof(int) * (size_t)chunk;
+    o_gbits = off = align256(off);
+    off += sizeof(unsigned long long) * (size_t)chunk;
+    o_list = off = align256(off);
+    off += sizeof(int32_t) * (size_t)chunk;
+    o_xs = off = align256(off);
+    off += tc_x_bytes(chunk);
+  }
+  if ((rc = h->grade.ensure(off)) != MTP_OK) return rc;
+  unsigned char* raw = h->grade.as<unsigned char>();
   double* base = h->grade.as<double>();
   unsigned long long* gmax_bits = reinterpret_cast<unsigned long long*>(base);
   unsigned long long* n_amb = gmax_bits + 1;
   double* cfg_out = base + 2;
+  unsigned long long* n_rchk = gmax_bits + 4;
+  unsigned* list_n = reinterpret_cast<unsigned*>(base + 5);
+  int* tc_status = reinterpret_cast<int*>(base + 6);
   double* amax = base + head;
   double* bsum = amax + m;
   double* rows = bsum + m;
@@ -218,9 +279,32 @@ extern "C" int mtp_compute_grade(mtp_handle* h, const mtp_nlist* nl, const doubl
     a.atom_begin = b;
     a.atom_end = b + cnt;
     if ((rc = h->ops->rows(a, nullptr, cnt, rows, m, a_inv_cfg ? bsum : nullptr, s)) != MTP_OK) return rc;
-    if (a_inv) {
+    if (tensor) {
+      auto* colmax = reinterpret_cast<unsigned long long*>(raw + o_colmax);
+      auto* dexp = reinterpret_cast<int*>(raw + o_dexp);
+      auto* fexp = reinterpret_cast<int*>(raw + o_fexp);
+      auto* fmax = reinterpret_cast<int*>(raw + o_fmax);
+      auto* ys = reinterpret_cast<uint16_t*>(raw + o_ys);
+      auto* erow = reinterpret_cast<int*>(raw + o_erow);
+      auto* gbits = reinterpret_cast<unsigned long long*>(raw + o_gbits);
+      auto* list = reinterpret_cast<int32_t*>(raw + o_list);
+      auto* xs = reinterpret_cast<uint16_t*>(raw + o_xs);
+      if ((rc = tc_prepare(rows, cnt, m, a_inv, amax, colmax, ys, fexp, dexp, fmax, xs, erow, tc_status, s)) !=
+          MTP_OK)
+        return rc;
+      if ((rc = tc_gemm(xs, ys, fexp, erow, cnt, gbits, tc_status, nullptr, s)) != MTP_OK) return rc;
+      MTP_TRY_CUDA(cudaMemsetAsync(list_n, 0, sizeof(unsigned), s));
+      if ((rc = tc_finalize(gbits, cnt, erow, fmax, tau_sel, tau_brk, gamma + b, flags + b, gmax_bits, list, list_n,
+                            s)) != MTP_OK)
+        return rc;
       gemm_grade_kernel<<<(unsigned)((cnt + kGemmBM - 1) / kGemmBM), 256, 0, s>>>(
-          rows, cnt, m, a_inv, amax, tau_sel, tau_brk, gamma + b, flags + b, gmax_bits, n_amb);
+          rows, cnt, m, a_inv, amax, tau_sel, tau_brk, gamma + b, flags + b, gmax_bits, n_amb, list, list_n);
+      MTP_TRY_CUDA(cudaGetLastError());
+      add_count_kernel<<<1, 1, 0, s>>>(n_rchk, list_n);
+      MTP_TRY_CUDA(cudaGetLastError());
+    } else if (a_inv) {
+      gemm_grade_kernel<<<(unsigned)((cnt + kGemmBM - 1) / kGemmBM), 256, 0, s>>>(
+          rows, cnt, m, a_inv, amax, tau_sel, tau_brk, gamma + b, flags + b, gmax_bits, n_amb, nullptr, nullptr);
       MTP_TRY_CUDA(cudaGetLastError());
     }
   }
@@ -228,23 +312,45 @@ extern "C" int mtp_compute_grade(mtp_handle* h, const mtp_nlist* nl, const doubl
     cfg_grade_kernel<<<1, 256, 0, s>>>(bsum, a_inv_cfg, m, cfg_out);
     MTP_TRY_CUDA(cudaGetLastError());
   }
-  double hostbuf[4] = {0, 0, 0, 0};
-  MTP_TRY_CUDA(cudaMemcpyAsync(hostbuf, base, sizeof(double) * 4, cudaMemcpyDeviceToHost, s));
+  double hostbuf[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+  MTP_TRY_CUDA(cudaMemcpyAsync(hostbuf, base, sizeof(double) * 8, cudaMemcpyDeviceToHost, s));
   MTP_TRY_CUDA(cudaStreamSynchronize(s));
-  unsigned long long gbits, amb;
-  std::memcpy(&gbits, &hostbuf[0], sizeof(gbits));
+  unsigned long long gbits_h, amb, rchk;
+  std::memcpy(&gbits_h, &hostbuf[0], sizeof(gbits_h));
   std::memcpy(&amb, &hostbuf[1], sizeof(amb));
+  std::memcpy(&rchk, &hostbuf[4], sizeof(rchk));
+  int tcs;
+  std::memcpy(&tcs, &hostbuf[6], sizeof(tcs));
+  if (tcs == MTP_ERR_TIMEOUT) {
+    set_error("mtp_compute_grade: a wait inside the tensor-core grade kernel gave up");
+    return MTP_ERR_TIMEOUT;
+  }
   double gmax;
-  std::memcpy(&gmax, &gbits, sizeof(gmax));
+  std::memcpy(&gmax, &gbits_h, sizeof(gmax));
   if (a_inv_cfg && std::fabs(hostbuf[2] - tau_sel) <= hostbuf[3]) ++amb;
   if (a_inv_cfg && std::fabs(hostbuf[2] - tau_brk) <= hostbuf[3]) ++amb;
   if (gamma_max) *gamma_max = a_inv ? gmax : 0.0;
   if (gamma_cfg) *gamma_cfg = a_inv_cfg ? hostbuf[2] : 0.0;
   if (n_ambiguous) *n_ambiguous = (int64_t)amb;
-  if (!std::isfinite(gmax) || (a_inv_cfg && !std::isfinite(hostbuf[2]))) {
+  if (n_rechecked) *n_rechecked = (int64_t)rchk;
+  if (!std::isfinite(gmax) || (a_inv_cfg && !std::isfinite(hostbuf[2])) || tcs == MTP_ERR_NONFINITE) {
     set_error("mtp_compute_grade: non-finite grade");
     return MTP_ERR_NONFINITE;
   }
   const double worst = std::max(a_inv ? gmax : 0.0, a_inv_cfg ? hostbuf[2] : 0.0);
   return worst > tau_brk ? MTP_STATUS_BREAK : MTP_OK;
+}
+
+// Verification hook for the tensor-core product (see mtp.h).
+extern "C" int mtp_grade_tc_selftest(const uint16_t* xs, const uint16_t* ys, const int32_t* fexp, const int32_t* erow,
+                                     int64_t n_rows, float* acc, uint64_t* gamma_bits, void* stream) {
+  if (n_rows < 0 || (n_rows > 0 && (!xs || !ys || !fexp || !erow || !gamma_bits))) {
+    set_error("mtp_grade_tc_selftest: NULL argument");
+    return MTP_ERR_ARG;
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  int rc = tc_gemm(xs, ys, fexp, erow, n_rows, reinterpret_cast<unsigned long long*>(gamma_bits), nullptr, acc, s);
+  if (rc != MTP_OK) return rc;
+  MTP_TRY_CUDA(cudaStreamSynchronize(s));
+  return MTP_OK;
 }

@@ -93,6 +93,20 @@ struct LevelEntry {
 
 const LevelEntry* find_level(int level);
 
+// Tensor-core grade (grade_tc.cu).
+constexpr int kTcSlices = 7;      // BF16 slices per operand
+constexpr int kTcMaxBasis = 128;  // padded basis size of the tensor-core product
+size_t tc_x_bytes(int64_t n_rows);
+size_t tc_y_bytes();
+int tc_prepare(const double* rows, int64_t n, int m, const double* a_inv, const double* amax,
+               unsigned long long* colmax, uint16_t* ys, int* fexp, int* dexp, int* fmax, uint16_t* xs, int* erow,
+               int* status, cudaStream_t s);
+int tc_gemm(const uint16_t* xs, const uint16_t* ys, const int* fexp, const int* erow, int64_t n,
+            unsigned long long* gbits, int* status, float* dbg, cudaStream_t s);
+int tc_finalize(const unsigned long long* gbits, int64_t n, const int* erow, const int* fmax, double tau_sel,
+                double tau_brk, double* gamma, uint8_t* flags, unsigned long long* gmax_bits, int32_t* list,
+                unsigned* list_n, cudaStream_t s);
+
 }  // namespace mtp
 
 struct mtp_handle {

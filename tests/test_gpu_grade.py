@@ -1,6 +1,9 @@
 """Extrapolation grade (neighbourhood and configuration mode) against the
-oracle: flags bit-exact, grades within 1e-7 relative (FP64 on both sides;
-the products cancel by ~5e7 on these active sets, so 1e-7 leaves a margin)."""
+oracle: flags bit-exact, grades within 1e-7 relative, for both products: the
+tensor-core method (error-free BF16 slicing, FP64 re-check near the
+thresholds) and the FP64 method.  The products cancel by ~5e7 on these
+active sets, so FP64 rounding alone reaches ~1e-8 relative; 1e-7 leaves a
+margin."""
 import json
 import os
 
@@ -35,7 +38,7 @@ def active():
     return np.array(d["a_inv"]).reshape(m, m), np.array(d["a_inv_cfg"]).reshape(m, m), d
 
 
-def run(P, st, a_inv, a_cfg):
+def run(P, st, a_inv, a_cfg, method=None, chunk_atoms=100):
     pot = P.Potential.from_dict(pot_dict("bcc-l16-s1"))
     x = torch.tensor(st.x, dtype=torch.float64, device="cuda")
     z = torch.tensor(st.z, dtype=torch.int32, device="cuda")
@@ -43,15 +46,19 @@ def run(P, st, a_inv, a_cfg):
     out = P.mtp_compute_grade(pot, nl, x, z, st.cell,
                               a_inv=torch.tensor(a_inv, device="cuda") if a_inv is not None else None,
                               a_inv_cfg=torch.tensor(a_cfg, device="cuda") if a_cfg is not None else None,
-                              tau_sel=TAU_SEL, tau_brk=TAU_BRK, chunk_atoms=100)
+                              tau_sel=TAU_SEL, tau_brk=TAU_BRK, chunk_atoms=chunk_atoms, method=method)
     torch.cuda.synchronize()
     return out
 
 
-def test_grade_matches_oracle_flags_bit_exact(P, active):
+@pytest.mark.parametrize("method,chunk", [("tensor", 100), ("tensor", 129), ("tensor", 0), ("fp64", 100)])
+def test_grade_matches_oracle_flags_bit_exact(P, active, method, chunk):
+    """300 atoms in chunks of 100 (one ragged tile each), 129 (a full tile and
+    a one-row tile) or one chunk."""
     a_inv, a_cfg, _ = active
     st = synth.crystal("bcc", (6, 5, 5), 3.16, 0.15, 1, 5)
-    out = run(P, st, a_inv, a_cfg)
+    meth = P.MTP_GRADE_TENSOR if method == "tensor" else P.MTP_GRADE_FP64
+    out = run(P, st, a_inv, a_cfg, method=meth, chunk_atoms=chunk)
     model = oracle_model("bcc-l16-s1")
     b = O.basis_matrix(model, st.x, st.z, st.cell, O.neighbor_list(st.x, st.cell, st.pbc, 5.0))
     gam = O.grade(b, a_inv)
@@ -63,6 +70,25 @@ def test_grade_matches_oracle_flags_bit_exact(P, active):
     assert out["gamma_cfg"] == pytest.approx(g_cfg, rel=1e-7)
     assert out["status"] == (1 if max(gam.max(), g_cfg) > TAU_BRK else 0)
     assert out["n_ambiguous"] == 0
+    # the tensor-core method re-checks exactly the rows within 5% of a threshold
+    near = (np.abs(gam - TAU_SEL) <= 0.05 * TAU_SEL) | (np.abs(gam - TAU_BRK) <= 0.05 * TAU_BRK)
+    if method == "tensor":
+        assert out["n_rechecked"] == int(near.sum())
+    else:
+        assert out["n_rechecked"] == 0
+
+
+def test_tensor_and_fp64_methods_agree(P, active):
+    """Both products on a 1,024-atom sigma = 0.15 A box: identical flags, grades
+    within 1e-7 relative of each other."""
+    a_inv, _, _ = active
+    st = synth.crystal("bcc", (8, 8, 8), 3.16, 0.15, 1, 5, sub=3)
+    t = run(P, st, a_inv, None, method=P.MTP_GRADE_TENSOR, chunk_atoms=0)
+    f = run(P, st, a_inv, None, method=P.MTP_GRADE_FP64, chunk_atoms=0)
+    gt, gf = t["gamma"].cpu().numpy(), f["gamma"].cpu().numpy()
+    assert np.all(np.abs(gt - gf) <= 1e-7 * gf)
+    assert np.array_equal(t["flags"].cpu().numpy(), f["flags"].cpu().numpy())
+    assert t["gamma_max"] == pytest.approx(f["gamma_max"], rel=1e-7)
 
 
 def test_grade_is_one_on_the_active_set_and_bounded_on_its_pool(P, active):
