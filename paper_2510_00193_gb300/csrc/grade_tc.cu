@@ -11,7 +11,7 @@
 // lower-precision matrices):
 //
 //   1. Column balancing (exact, powers of two): C = b A^-1 = (b D)(D^-1 A^-1)
-//      with d_j = 2^round((log2 max_k|A^-1_jk| - log2 max_i|b_ij|) / 2).
+//      with d_j = 2^((ilogb max_k|A^-1_jk| - ilogb max_i|b_ij|) / 2).
 //   2. Row/column scaling: x_ij = b_ij d_j 2^-e_i with |x| <= 1 per row,
 //      y_jk = A^-1_jk / d_j 2^-f_k with |y| <= 1 per column.
 //   3. Slices: x = sum_{s=1..7} 2^-8s X_s + rho, each X_s an integer matrix
@@ -104,10 +104,52 @@ static_assert(kSmTotal <= kSmAlloc, "shared-memory map exceeds the allocation");
 
 constexpr int kBadRow = INT_MAX;   // erow sentinel: non-finite basis row
 
-__device__ __forceinline__ uint16_t bf16_of_int(double q) {
-  // |q| <= 256 is an integer: FP32 holds it exactly and its upper 16 bits are
-  // the BF16 encoding (at most 8 significant bits).
-  return (uint16_t)(__float_as_uint((float)q) >> 16);
+// BF16 encoding of an integer |q| <= 256 (at most 8 significant bits, so
+// exact): the integer enters the mantissa of 1.5 * 2^23 (exact for
+// |q| < 2^22, no conversion instruction) and the upper 16 bits of the FP32
+// value are its BF16 encoding.
+__device__ __forceinline__ uint32_t bf16_of_int(int q) {
+  return __float_as_uint(__int_as_float(0x4B400000 + q) - 12582912.0f) >> 16;
+}
+
+// floor(log2 |b|) from the IEEE fields (b finite and nonzero).
+__device__ __forceinline__ int ilog2_bits(long long bits) {
+  const int E = (int)((bits >> 52) & 0x7FF);
+  if (E != 0) return E - 1023;
+  const long long M = bits & 0xFFFFFFFFFFFFFll;
+  return (63 - __clzll(M)) - 1074;
+}
+
+// F = round(b 2^shift) as an integer (halves away from zero), straight from
+// the IEEE fields; the caller guarantees |b| 2^shift <= 2^56.
+__device__ __forceinline__ long long fixed_round(double b, int shift) {
+  const long long bits = __double_as_longlong(b);
+  const int E = (int)((bits >> 52) & 0x7FF);
+  long long M = bits & 0xFFFFFFFFFFFFFll;
+  int ex = -1074;
+  if (E != 0) {
+    M |= 1ll << 52;
+    ex = E - 1075;
+  }
+  const int sh = ex + shift;   // |F| = M 2^sh
+  long long F;
+  if (sh >= 0) F = M << sh;
+  else if (sh > -63) F = (M + (1ll << (-sh - 1))) >> (-sh);
+  else F = 0;
+  return bits < 0 ? -F : F;
+}
+
+// Balanced base-256 digits of F (|F| <= 2^56): F = sum_{s=1..7} q_s 2^(8(7-s)),
+// q_7..q_2 in [-128, 127] (the digit of least weight first), |q_1| <= 256;
+// returned as BF16 encodings, q[s-1] for slice s.
+__device__ __forceinline__ void balanced_digits(long long F, uint32_t (&q)[kTcSlices]) {
+#pragma unroll
+  for (int s = kTcSlices - 1; s >= 1; --s) {
+    const int dig = (int)((F + 128) & 255) - 128;
+    q[s] = bf16_of_int(dig);
+    F = (F - dig) >> 8;   // exact: F - dig is a multiple of 256
+  }
+  q[0] = bf16_of_int((int)F);
 }
 
 __device__ __forceinline__ void set_status(int* status, int code) {
@@ -128,61 +170,54 @@ __global__ void tc_colmax_kernel(const double* __restrict__ rows, int64_t n, int
   atomicMax(colmax + j, (unsigned long long)__double_as_longlong(v));
 }
 
-// Balancing exponents d_j, column exponents f_k and the BF16 slices of
-// y = D^-1 A^-1 2^-f, written as [half][t][64 x 128] in the Y layout.  One
-// block of 128 threads; m <= 128.
-__global__ void tc_prep_y_kernel(const double* __restrict__ a_inv, int m, const double* __restrict__ amax,
-                                 const unsigned long long* __restrict__ colmax, uint16_t* __restrict__ ys,
-                                 int* __restrict__ fexp, int* __restrict__ dexp, int* __restrict__ fmax_out,
-                                 int* status) {
-  __shared__ int s_dexp[kTcK];
-  __shared__ int s_fmax;
-  const int t = threadIdx.x;
-  if (t == 0) s_fmax = INT_MIN;
-  if (t < kTcK) {
-    int d = 0;
-    if (t < m) {
-      const double bm = __longlong_as_double((long long)colmax[t]);
-      const double am = amax[t];
-      if (bm > 0.0 && am > 0.0 && isfinite(bm) && isfinite(am)) d = (ilogb(am) - ilogb(bm)) / 2;
-    }
-    s_dexp[t] = d;
-    dexp[t] = d;
+// Balancing exponents d_j = (ilogb max_k|A^-1_jk| - ilogb max_i|b_ij|) / 2
+// (one thread per basis function j).
+__global__ void tc_dexp_kernel(const double* __restrict__ amax, const unsigned long long* __restrict__ colmax, int m,
+                               int* __restrict__ dexp) {
+  const int j = threadIdx.x;
+  if (j >= kTcK) return;
+  int d = 0;
+  if (j < m) {
+    const double bm = __longlong_as_double((long long)colmax[j]);
+    const double am = amax[j];
+    if (bm > 0.0 && am > 0.0 && isfinite(bm) && isfinite(am)) d = (ilogb(am) - ilogb(bm)) / 2;
   }
+  dexp[j] = d;
+}
+
+// Column exponent f_k (|A^-1_jk| 2^(-d_j - f_k) < 1 for all j) and the BF16
+// slices of y_jk = A^-1_jk 2^(-d_j - f_k), written as [half][t][64 x 128] in
+// the Y layout.  One block per column k, one thread per row j.
+__global__ void __launch_bounds__(kTcK) tc_prep_y_kernel(const double* __restrict__ a_inv, int m,
+                                                         const int* __restrict__ dexp, uint16_t* __restrict__ ys,
+                                                         int* __restrict__ fexp, int* __restrict__ fmax_out,
+                                                         int* status) {
+  __shared__ int s_lg;
+  const int k = blockIdx.x, j = threadIdx.x;
+  if (j == 0) s_lg = INT_MIN;
   __syncthreads();
-  if (t < kTcK) {
-    const int k = t;
-    int f = 0;
-    if (k < m) {
-      double mx = 0.0;
-      bool finite = true;
-      for (int j = 0; j < m; ++j) {
-        const double y = ldexp(a_inv[(int64_t)j * m + k], -s_dexp[j]);
-        finite = finite && isfinite(y);
-        mx = fmax(mx, fabs(y));
-      }
-      if (!finite) set_status(status, MTP_ERR_NONFINITE);
-      f = (mx > 0.0 && finite) ? ilogb(mx) + 1 : 0;
-      atomicMax(&s_fmax, f);
-    }
+  double v = 0.0;
+  bool finite = true;
+  if (k < m && j < m) {
+    v = a_inv[(int64_t)j * m + k];
+    finite = isfinite(v);
+    if (!finite) v = 0.0;
+    if (v != 0.0) atomicMax(&s_lg, ilog2_bits(__double_as_longlong(v)) - dexp[j]);
+  }
+  if (!finite) set_status(status, MTP_ERR_NONFINITE);
+  __syncthreads();
+  const int f = (s_lg == INT_MIN) ? 0 : s_lg + 1;
+  if (j == 0) {
     fexp[k] = f;
-    const int half = k / kTcN, kl = k % kTcN;
-    for (int j = 0; j < kTcK; ++j) {
-      double w = 0.0;
-      if (k < m && j < m) {
-        w = ldexp(a_inv[(int64_t)j * m + k], -s_dexp[j] - f);
-        if (!isfinite(w)) w = 0.0;
-      }
-#pragma unroll
-      for (int s = 0; s < kTcS; ++s) {
-        const double q = rint(ldexp(w, 8 * (s + 1)));
-        w -= ldexp(q, -8 * (s + 1));   // exact (Sterbenz): the residual halves the unit
-        ys[(int64_t)(half * kTcS + s) * (kTcN * kTcK) + y_elem(kl, j)] = bf16_of_int(q);
-      }
-    }
+    if (k < m) atomicMax(fmax_out, f);
   }
-  __syncthreads();
-  if (t == 0) *fmax_out = (s_fmax == INT_MIN) ? 0 : s_fmax;
+  long long F = 0;
+  if (v != 0.0) F = fixed_round(v, 56 - dexp[j] - f);
+  uint32_t q[kTcS];
+  balanced_digits(F, q);
+  const int half = k / kTcN, kl = k % kTcN;
+#pragma unroll
+  for (int s = 0; s < kTcS; ++s) ys[(int64_t)(half * kTcS + s) * (kTcN * kTcK) + y_elem(kl, j)] = (uint16_t)q[s];
 }
 
 // Row exponents e_i and the BF16 slices of x = b D 2^-e, written as
@@ -202,36 +237,34 @@ __global__ void __launch_bounds__(kTcM) tc_split_x_kernel(const double* __restri
   int e = 0;
   bool bad = false;
   if (valid) {
-    double mx = 0.0;
+    // e_i = 1 + max_j floor(log2 |b_ij 2^d_j|), so that |x_ij| < 1
+    int mx = INT_MIN;
     for (int j = 0; j < m; ++j) {
-      const double v = row[j];
-      if (!isfinite(v)) bad = true;
-      mx = fmax(mx, fabs(ldexp(v, s_dexp[j])));
+      const long long bits = __double_as_longlong(row[j]);
+      if (((bits >> 52) & 0x7FF) == 0x7FF) bad = true;
+      if ((bits & 0x7FFFFFFFFFFFFFFFll) != 0) mx = max(mx, ilog2_bits(bits) + s_dexp[j]);
     }
-    e = (mx > 0.0 && !bad) ? ilogb(mx) + 1 : 0;
+    e = (mx == INT_MIN || bad) ? 0 : mx + 1;
     erow[r] = bad ? kBadRow : e;
   }
   uint16_t* base = xs + tile * (int64_t)kTcS * (kTcM * kTcK);
   for (int jc = 0; jc < kTcK / 8; ++jc) {
-    double w[8];
+    uint32_t q[8][kTcS];
 #pragma unroll
     for (int u = 0; u < 8; ++u) {
       const int j = jc * 8 + u;
-      w[u] = (valid && !bad && j < m) ? ldexp(row[j], s_dexp[j] - e) : 0.0;
+      long long F = 0;
+      if (valid && !bad && j < m) {
+        const double v = row[j];
+        if (v != 0.0) F = fixed_round(v, s_dexp[j] - e + 56);
+      }
+      balanced_digits(F, q[u]);
     }
 #pragma unroll
     for (int s = 0; s < kTcS; ++s) {
-      uint32_t packed[4];
-#pragma unroll
-      for (int u = 0; u < 8; u += 2) {
-        const double q0 = rint(ldexp(w[u], 8 * (s + 1)));
-        const double q1 = rint(ldexp(w[u + 1], 8 * (s + 1)));
-        w[u] -= ldexp(q0, -8 * (s + 1));
-        w[u + 1] -= ldexp(q1, -8 * (s + 1));
-        packed[u / 2] = (uint32_t)bf16_of_int(q0) | ((uint32_t)bf16_of_int(q1) << 16);
-      }
       *reinterpret_cast<uint4*>(base + (int64_t)s * (kTcM * kTcK) + x_elem(il, jc * 8)) =
-          make_uint4(packed[0], packed[1], packed[2], packed[3]);
+          make_uint4(q[0][s] | (q[1][s] << 16), q[2][s] | (q[3][s] << 16), q[4][s] | (q[5][s] << 16),
+                     q[6][s] | (q[7][s] << 16));
     }
   }
 }
@@ -439,27 +472,43 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_grade_kernel(const TcGemmArg
 
 // Per-row decision: grades clear of both thresholds by more than
 // max(0.05 tau, bound) take their flags here; the others are listed for the
-// FP64 re-check.
-__global__ void tc_finalize_kernel(const unsigned long long* __restrict__ gbits, int64_t n,
-                                   const int* __restrict__ erow, const int* __restrict__ fexp_max, double tau_sel,
-                                   double tau_brk, double* __restrict__ gamma, uint8_t* __restrict__ flags,
-                                   unsigned long long* __restrict__ gmax_bits, int32_t* __restrict__ list,
-                                   unsigned* __restrict__ list_n) {
+// FP64 re-check.  List appends and the running maximum are aggregated per
+// warp (one atomic each).
+__global__ void __launch_bounds__(256) tc_finalize_kernel(const unsigned long long* __restrict__ gbits, int64_t n,
+                                                          const int* __restrict__ erow,
+                                                          const int* __restrict__ fexp_max, double tau_sel,
+                                                          double tau_brk, double* __restrict__ gamma,
+                                                          uint8_t* __restrict__ flags,
+                                                          unsigned long long* __restrict__ gmax_bits,
+                                                          int32_t* __restrict__ list, unsigned* __restrict__ list_n) {
   const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (r >= n) return;
-  const double g = __longlong_as_double((long long)gbits[r]);
-  const int e = erow[r];
-  gamma[r] = g;
-  const double bound = (e == kBadRow) ? 0.0 : ldexp(1.0, e + *fexp_max - 47) + ldexp(g, -52);
-  const bool near = !isfinite(g) || fabs(g - tau_sel) <= fmax(0.05 * tau_sel, bound) ||
-                    fabs(g - tau_brk) <= fmax(0.05 * tau_brk, bound);
-  if (near) {
-    const unsigned k = atomicAdd(list_n, 1u);
-    list[k] = (int32_t)r;
-  } else {
-    flags[r] = (uint8_t)((g > tau_sel ? 1 : 0) | (g > tau_brk ? 2 : 0));
-    atomicMax(gmax_bits, (unsigned long long)__double_as_longlong(g));
+  const int lane = threadIdx.x & 31;
+  const bool in = r < n;
+  double g = 0.0;
+  bool near = false;
+  if (in) {
+    g = __longlong_as_double((long long)gbits[r]);
+    const int e = erow[r];
+    gamma[r] = g;
+    // 2^(e + F - 47) + 2^-52 g; exponents clamped to the normal range
+    const int pe = (e == kBadRow) ? -1023 : max(-1022, min(1023, e + *fexp_max - 47));
+    const double bound = (pe <= -1023) ? 0.0 : __longlong_as_double((long long)(pe + 1023) << 52) + g * 0x1p-52;
+    near = !isfinite(g) || fabs(g - tau_sel) <= fmax(0.05 * tau_sel, bound) ||
+           fabs(g - tau_brk) <= fmax(0.05 * tau_brk, bound);
+    if (!near) flags[r] = (uint8_t)((g > tau_sel ? 1 : 0) | (g > tau_brk ? 2 : 0));
   }
+  const unsigned listed = __ballot_sync(0xffffffffu, in && near);
+  if (listed) {
+    const int leader = __ffs(listed) - 1;
+    unsigned base = 0;
+    if (lane == leader) base = atomicAdd(list_n, (unsigned)__popc(listed));
+    base = __shfl_sync(0xffffffffu, base, leader);
+    if (in && near) list[base + __popc(listed & ((1u << lane) - 1u))] = (int32_t)r;
+  }
+  double gm = (in && !near) ? g : 0.0;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) gm = fmax(gm, __shfl_down_sync(0xffffffffu, gm, o));
+  if (lane == 0 && gm > 0.0) atomicMax(gmax_bits, (unsigned long long)__double_as_longlong(gm));
 }
 
 // ---------------------------------------------------------------------------
@@ -496,7 +545,10 @@ int tc_prepare(const double* rows, int64_t n, int m, const double* a_inv, const 
   const int grid = (int)std::min<int64_t>(n, 4 * (int64_t)sm_count());
   tc_colmax_kernel<<<grid, kTcK, 0, s>>>(rows, n, m, colmax);
   MTP_TC_CHECK("tc_colmax_kernel");
-  tc_prep_y_kernel<<<1, kTcK, 0, s>>>(a_inv, m, amax, colmax, ys, fexp, dexp, fmax, status);
+  tc_dexp_kernel<<<1, kTcK, 0, s>>>(amax, colmax, m, dexp);
+  MTP_TC_CHECK("tc_dexp_kernel");
+  MTP_TRY_CUDA(cudaMemsetAsync(fmax, 0x80, sizeof(int), s));   // INT_MIN-like start for the maximum
+  tc_prep_y_kernel<<<kTcK, kTcK, 0, s>>>(a_inv, m, dexp, ys, fexp, fmax, status);
   MTP_TC_CHECK("tc_prep_y_kernel");
   const int64_t tiles = (n + kTcM - 1) / kTcM;
   tc_split_x_kernel<<<(unsigned)tiles, kTcM, 0, s>>>(rows, n, m, dexp, xs, erow);
