@@ -149,15 +149,15 @@ def run_grade(P, torch, args):
     with open(os.path.join(ROOT, "potentials", "bcc-l16-s1-active.json")) as fh:
         act = json.load(fh)
     m = act["m"]
-    st = synth.crystal("bcc", (50, 50, 100), 3.16, 0.15, 1, 5)
+    st = synth.crystal("bcc", (50, 50, args.grade_cells), 3.16, 0.15, 1, 5)
     pot = P.Potential.from_file(os.path.join(ROOT, "potentials", "bcc-l16-s1.json"))
     x = torch.tensor(st.x, dtype=torch.float64, device="cuda")
     z = torch.tensor(st.z, dtype=torch.int32, device="cuda")
     a_inv = torch.tensor(act["a_inv"], dtype=torch.float64, device="cuda").reshape(m, m)
     a_cfg = torch.tensor(act["a_inv_cfg"], dtype=torch.float64, device="cuda").reshape(m, m)
     nl = P.mtp_build_neighbors(pot, x, st.cell, st.pbc)
-    res = {"workload": "bcc-50x50x100 (500,000 atoms), level 16, 1 species, sigma 0.15 A; active sets by MaxVol",
-           "unit": UNIT}
+    res = {"workload": "bcc-50x50x%d (%d atoms), level 16, 1 species, sigma 0.15 A; active sets by MaxVol"
+                       % (args.grade_cells, st.n), "unit": UNIT}
     flops_fp64 = 2.0 * st.n * m * m
     for name, method in (("tensor", P.MTP_GRADE_TENSOR), ("fp64", P.MTP_GRADE_FP64)):
         out = P.mtp_compute_grade(pot, nl, x, z, st.cell, a_inv=a_inv, a_inv_cfg=a_cfg, method=method)
@@ -183,7 +183,42 @@ def run_grade(P, torch, args):
     res["ms_per_step"] = res["tensor"]["ms_per_step"]
     res["product_flops_fp64_equivalent"] = flops_fp64
     res["mma_flops_executed"] = 2.0 * 28 * 128 * 128 * 128 * ((st.n + 127) // 128)
+    res["tc_kernel"] = time_tc_kernel(P, torch)
     return res
+
+
+def time_tc_kernel(P, torch, rows=262144, reps=5):
+    """The tensor-core grade kernel alone (through the C-ABI verification hook)
+    on random BF16 slices of one full 262,144-row chunk: device time per
+    launch and executed MMA throughput against the measured BF16 peak."""
+    g = torch.Generator(device="cuda").manual_seed(20251009)
+    tiles = (rows + 127) // 128
+    xs = torch.randint(-128, 129, (tiles * 7 * 128 * 128,), device="cuda", generator=g, dtype=torch.int32)
+    ys = torch.randint(-128, 129, (2 * 7 * 64 * 128,), device="cuda", generator=g, dtype=torch.int32)
+    # integers -> BF16 bit patterns (exact: at most 8 significant bits)
+    to_bf16 = lambda t: (t.to(torch.float32).view(torch.int32) >> 16).to(torch.int16)
+    xs, ys = to_bf16(xs), to_bf16(ys)
+    fexp = torch.zeros(128, dtype=torch.int32, device="cuda")
+    erow = torch.zeros(rows, dtype=torch.int32, device="cuda")
+    P.mtp_grade_tc_selftest(xs, ys, fexp, erow, rows)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    times = []
+    for _ in range(reps):
+        e0.record()
+        P.mtp_grade_tc_selftest(xs, ys, fexp, erow, rows)
+        e1.record()
+        torch.cuda.synchronize()
+        times.append(e0.elapsed_time(e1))
+    ms = min(times)
+    flops = 2.0 * 28 * 128 * 128 * 128 * tiles
+    peak = 1881.0
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as fh:
+            peak = json.load(fh).get("bf16_tflops", peak)
+    return {"rows": rows, "ms": ms, "mma_tflops": flops / (ms * 1e-3) / 1e12, "bf16_peak_tflops": peak,
+            "frac": flops / (ms * 1e-3) / 1e12 / peak}
 
 
 def run_batch(P, torch, args):
@@ -479,6 +514,8 @@ def main():
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 comparison steps")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end steps")
     ap.add_argument("--no-grade", action="store_true", help="skip the extrapolation-grade workload")
+    ap.add_argument("--grade-cells", type=int, default=100,
+                    help="BCC cells along c of the grade box (50 x 50 x this; 100: the 500,000-atom workload)")
     ap.add_argument("--no-batch", action="store_true", help="skip the 4096-configuration batch workload")
     ap.add_argument("--no-diff", action="store_true", help="skip the level-20 differentiation workload")
     ap.add_argument("--cells", type=int, default=CELLS[0], help="BCC cells per edge (80: the 1,024,000-atom "

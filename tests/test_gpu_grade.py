@@ -126,3 +126,30 @@ def test_full_size_config5_sampled(P, active):
     assert np.array_equal(flags[centres], O.grade_flags(gam, TAU_SEL, TAU_BRK))
     # rows whose FP64 grade lies within its own error bound of a threshold
     assert out["n_ambiguous"] <= 1e-3 * st.n
+
+
+def test_level8_grade_padding_and_one_row_chunks(P):
+    """Level-8 potential (m = 9: the tensor-core operands are mostly padding)
+    with an active set chosen by the oracle's MaxVol on a 128-atom sigma =
+    0.05 A box, evaluated on a 250-atom sigma = 0.15 A box in one chunk and in
+    chunks of one row; flags bit-exact, grades within 1e-7 relative."""
+    model = oracle_model("bcc-l8-s1")
+    pool_st = synth.crystal("bcc", (4, 4, 4), 3.16, 0.05, 1, 11)
+    pool = O.basis_matrix(model, pool_st.x, pool_st.z, pool_st.cell,
+                          O.neighbor_list(pool_st.x, pool_st.cell, pool_st.pbc, 5.0))
+    rows, a_inv, _ = O.maxvol(pool, delta=0.01)
+    st = synth.crystal("bcc", (5, 5, 5), 3.16, 0.15, 1, 12)
+    b = O.basis_matrix(model, st.x, st.z, st.cell, O.neighbor_list(st.x, st.cell, st.pbc, 5.0))
+    gam = O.grade(b, a_inv)
+    pot = P.Potential.from_dict(pot_dict("bcc-l8-s1"))
+    x = torch.tensor(st.x, dtype=torch.float64, device="cuda")
+    z = torch.tensor(st.z, dtype=torch.int32, device="cuda")
+    nl = P.mtp_build_neighbors(pot, x, st.cell, st.pbc)
+    for method in (P.MTP_GRADE_TENSOR, P.MTP_GRADE_FP64):
+        for chunk in (0, 1):
+            out = P.mtp_compute_grade(pot, nl, x, z, st.cell, a_inv=torch.tensor(a_inv, device="cuda"),
+                                      tau_sel=TAU_SEL, tau_brk=TAU_BRK, chunk_atoms=chunk, method=method)
+            torch.cuda.synchronize()
+            got = out["gamma"].cpu().numpy()
+            assert np.all(np.abs(got - gam) <= 1e-7 * gam), (method, chunk)
+            assert np.array_equal(out["flags"].cpu().numpy(), O.grade_flags(gam, TAU_SEL, TAU_BRK))
