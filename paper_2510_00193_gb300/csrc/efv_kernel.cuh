@@ -27,6 +27,13 @@ __device__ __forceinline__ double warp_sum(double v) {
   return v;
 }
 
+__device__ __forceinline__ float warp_sum_r(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  return v;
+}
+__device__ __forceinline__ double warp_sum_r(double v) { return warp_sum(v); }
+
 __device__ __forceinline__ void flag_status(int* status, int code) {
   if (status) atomicCAS(status, 0, code);
 }
@@ -289,16 +296,21 @@ struct EfvShared {
 
 // Everything one centre atom contributes: its site energy (also stored in
 // e_atom), its force terms (scattered), its virial terms (w) and, with
-// DTHETA, its basis values (Bv) and radial-coefficient gradient (shared
+// DTHETA, its basis values and radial-coefficient gradient (shared
 // accumulators).  `cell` holds the rows of its configuration's cell.
+// Every lane of the warp calls this (the basis values are summed across the
+// warp right after the contraction, which frees their registers for the
+// second sweep): a lane without an atom passes active = false and a valid
+// atom index i, runs no pairs, writes nothing and contributes zeros (every
+// basis function vanishes at zero moments).
 template <class LV, class R, bool DTHETA>
 __device__ __forceinline__ void efv_atom(const EfvArgs& a, const EfvShared<R, LV::NMU, DTHETA>& sm, int64_t i,
-                                         const R* cell, double& e_i, R* w, R* Bv) {
+                                         bool active, const R* cell, double& e_i, R* w) {
   constexpr int NMU = LV::NMU;
   PairGeom<R> geom;
   geom.load_centre(a, i, cell);
   const int zi = __ldg(a.z + i);
-  const int64_t beg = __ldg(a.offsets + i), end = __ldg(a.offsets + i + 1);
+  const int64_t beg = active ? __ldg(a.offsets + i) : 0, end = active ? __ldg(a.offsets + i + 1) : 0;
   R M[LV::NCOMP];
 #pragma unroll
   for (int c = 0; c < LV::NCOMP; ++c) M[c] = R(0);
@@ -318,19 +330,32 @@ __device__ __forceinline__ void efv_atom(const EfvArgs& a, const EfvShared<R, LV
     LV::template moments<R>(M, f, dx * rinv, dy * rinv, dz * rinv);
   }
   R D[LV::NCOMP];
+  R Bv[DTHETA ? LV::NBASIS : 1];
   const R ei = LV::template contract<R, DTHETA>(M, sm.xi, D, Bv);
-  e_i = a.species_energy[zi] + (double)ei;
-  a.e_atom[i] = e_i;
+  if (DTHETA) {
+    // warp sums of the basis values (dE/dxi), in R: the block accumulator is
+    // in R, and FP64 shuffles of 100+ values would occupy the FP64 pipe
+    // longer than the atoms' own work on the mixed path
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int t = 0; t < (DTHETA ? LV::NBASIS : 1); ++t) {
+      const R v = warp_sum_r(active ? Bv[t] : R(0));
+      if (lane == 0) atomicAdd(sm.dxi + t, v);
+    }
+  }
+  e_i = active ? a.species_energy[zi] + (double)ei : 0.0;
+  if (active) a.e_atom[i] = e_i;
 
   R fx = R(0), fy = R(0), fz = R(0);
   // dE/dc contributions of this atom's pairs, summed per neighbour species in
   // thread-private memory and added to the block's shared accumulators once
   // per atom (per-pair shared atomics collide heavily between lanes)
+  // (packed [zj][mu][k] with the runtime n_q, so only S NMU n_q entries are touched)
   constexpr int kAccS = 4;
   const bool own_acc = DTHETA && sm.S <= kAccS;
   R acc[DTHETA ? kAccS * NMU * kMaxQ : 1];
   if (own_acc) {
-    for (int t = 0; t < sm.S * NMU * kMaxQ; ++t) acc[t] = R(0);
+    for (int t = 0; t < sm.S * NMU * sm.nq; ++t) acc[t] = R(0);
   }
   ps.start(a, geom, beg, end);
   while (ps.next(a, geom, j, img, lj)) {
@@ -354,12 +379,12 @@ __device__ __forceinline__ void efv_atom(const EfvArgs& a, const EfvShared<R, LV
     w[5] = fmadd(R(-0.5), fmadd(gy, dz, gz * dy), w[5]);
     if (DTHETA) {
       if (own_acc) {
-        R* dst = acc + zj * NMU * kMaxQ;
+        R* dst = acc + zj * NMU * sm.nq;
 #pragma unroll
         for (int mu = 0; mu < NMU; ++mu) {
 #pragma unroll
           for (int kk = 0; kk < kMaxQ; ++kk)
-            if (kk < sm.nq) dst[mu * kMaxQ + kk] = fmadd(q[kk], Smu[mu], dst[mu * kMaxQ + kk]);
+            if (kk < sm.nq) dst[mu * sm.nq + kk] = fmadd(q[kk], Smu[mu], dst[mu * sm.nq + kk]);
         }
       } else {
         R* dst = sm.dc + (zi * sm.S + zj) * NMU * sm.nq;
@@ -372,11 +397,11 @@ __device__ __forceinline__ void efv_atom(const EfvArgs& a, const EfvShared<R, LV
       }
     }
   }
+  if (!active) return;
   if (own_acc) {
     for (int zj = 0; zj < sm.S; ++zj) {
       R* dst = sm.dc + (zi * sm.S + zj) * NMU * sm.nq;
-      for (int mu = 0; mu < NMU; ++mu)
-        for (int kk = 0; kk < sm.nq; ++kk) atomicAdd(dst + mu * sm.nq + kk, acc[(zj * NMU + mu) * kMaxQ + kk]);
+      for (int t = 0; t < NMU * sm.nq; ++t) atomicAdd(dst + t, acc[zj * NMU * sm.nq + t]);
     }
   }
   scatter_force(a, i, fx, fy, fz);
@@ -390,7 +415,7 @@ __device__ __forceinline__ void efv_atom(const EfvArgs& a, const EfvShared<R, LV
 // Must be reached by every thread of the block.
 template <class LV, class R, bool DTHETA>
 __device__ __forceinline__ void efv_block_flush(const EfvShared<R, LV::NMU, DTHETA>& sm, double e_i, const R* w,
-                                                const R* Bv, double* e_out, double* w_out, double* theta_out) {
+                                                double* e_out, double* w_out, double* theta_out) {
   constexpr int NMU = LV::NMU;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int nwarps = (blockDim.x + 31) >> 5;
@@ -400,13 +425,6 @@ __device__ __forceinline__ void efv_block_flush(const EfvShared<R, LV::NMU, DTHE
   if (lane == 0) {
 #pragma unroll
     for (int t = 0; t < 7; ++t) sm.red[warp * 8 + t] = vals[t];
-  }
-  if (DTHETA) {
-#pragma unroll
-    for (int t = 0; t < (DTHETA ? LV::NBASIS : 1); ++t) {
-      const double v = warp_sum((double)Bv[t]);
-      if (lane == 0) atomicAdd(sm.dxi + t, R(v));
-    }
   }
   __syncthreads();
   if (threadIdx.x < 7) {
@@ -438,11 +456,10 @@ __global__ void __launch_bounds__(kEfvThreads) efv_kernel(const EfvArgs a) {
   const int64_t i = a.atom_begin + (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   double e_i = 0.0;
   R w[6] = {R(0), R(0), R(0), R(0), R(0), R(0)};
-  R Bv[DTHETA ? LV::NBASIS : 1];
-#pragma unroll
-  for (int t = 0; t < (DTHETA ? LV::NBASIS : 1); ++t) Bv[t] = R(0);
-  if (i < a.atom_end) efv_atom<LV, R, DTHETA>(a, sm, i, cell_of<R>(a), e_i, w, Bv);
-  efv_block_flush<LV, R, DTHETA>(sm, e_i, w, Bv, a.e_total, a.virial, a.dtheta);
+  const bool active = i < a.atom_end;
+  if (__any_sync(0xffffffffu, active))   // warp-uniform: whole warps without atoms skip the work
+    efv_atom<LV, R, DTHETA>(a, sm, active ? i : a.atom_begin, active, cell_of<R>(a), e_i, w);
+  efv_block_flush<LV, R, DTHETA>(sm, e_i, w, a.e_total, a.virial, a.dtheta);
 }
 
 template <class LV, class R, bool DTHETA>
