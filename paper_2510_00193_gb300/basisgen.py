@@ -393,6 +393,14 @@ class Level:
         self.comp_index = {c: i for i, c in enumerate(self.comps)}
         self.dag = Dag()
         self.roots = [self.dag.graph(g) for g in self.graphs]
+        # levels with an interpreted contraction sweep the neighbours once per
+        # component group (mu = 0 / mu >= 1), so that a group's moments or
+        # adjoints fit in registers
+        if level >= INTERPRET_FROM_LEVEL and self.nmu > 1:
+            self.groups = [[c for c, (mu, K) in enumerate(self.comps) if mu == 0],
+                           [c for c, (mu, K) in enumerate(self.comps) if mu >= 1]]
+        else:
+            self.groups = [list(range(len(self.comps)))]
 
     @property
     def m(self):
@@ -487,18 +495,21 @@ def _monomial_order(maxnu):
     return [K for nu in range(0, maxnu + 1) for K in multi_indices(nu)]
 
 
-def emit_moments(lv: Level):
-    """M[c] += f[mu] * u^K for every component (mu, K).  Each monomial is
-    formed and consumed at once, so few monomials are live at a time."""
+def emit_moments(lv: Level, subset=None, fname="moments"):
+    """M[c] += f[mu] * u^K for every component (mu, K) (of ``subset`` if
+    given).  Each monomial is formed and consumed at once, so few monomials
+    are live at a time."""
     L = []
     ind = "    "
     L.append("  template <class R>")
-    L.append("  __device__ __forceinline__ static void moments(R* __restrict__ M, const R* __restrict__ f, R ux, R uy, R uz) {")
+    L.append("  __device__ __forceinline__ static void %s(R* __restrict__ M, const R* __restrict__ f, R ux, R uy, R uz) {"
+             % fname)
     L.append(ind + "const R u000 = R(1);")
     by_k = defaultdict(list)
     for c, (mu, K) in enumerate(lv.comps):
-        by_k[K].append((c, mu))
-    for K in _monomial_order(max(lv.nu_max)):
+        if subset is None or c in subset:
+            by_k[K].append((c, mu))
+    for K in _monomial_order(max(sum(K) for K in by_k)):
         if sum(K) > 0:
             src, co = _monomial_source(K)
             L.append(ind + "const R %s = %s * %s;" % (_mono_name(K), _mono_name(src), co))
@@ -511,7 +522,7 @@ def emit_moments(lv: Level):
     return L
 
 
-def emit_pair_adjoint(lv: Level):
+def emit_pair_adjoint(lv: Level, subset=None, fname="pair_adjoint"):
     """Gradient of sum_c D[c] M_c(r) with respect to the pair vector r, where
     M_c(r) = f_mu(|r|) rhat^K:
 
@@ -526,10 +537,11 @@ def emit_pair_adjoint(lv: Level):
     L = []
     ind = "    "
     L.append("  template <class R>")
-    L.append("  __device__ __forceinline__ static void pair_adjoint(const R* __restrict__ D, const R* __restrict__ f, "
-             "const R* __restrict__ df, R ux, R uy, R uz, R rinv, R& gx, R& gy, R& gz, R* __restrict__ S) {")
+    L.append("  __device__ __forceinline__ static void %s(const R* __restrict__ D, const R* __restrict__ f, "
+             "const R* __restrict__ df, R ux, R uy, R uz, R rinv, R& gx, R& gy, R& gz, R* __restrict__ S) {" % fname)
     L.append(ind + "const R u000 = R(1);")
-    comp = lv.comp_index
+    comp = {key: c for key, c in lv.comp_index.items() if subset is None or c in subset}
+    comps = [key for c, key in enumerate(lv.comps) if subset is None or c in subset]
     declared = set()
 
     def acc(name, x, y):
@@ -539,7 +551,7 @@ def emit_pair_adjoint(lv: Level):
             declared.add(name)
             L.append(ind + "R %s = %s * %s;" % (name, x, y))
 
-    maxnu = max(lv.nu_max)
+    maxnu = max(sum(K) for _, K in comps)
     for J in _monomial_order(maxnu):
         if sum(J) > 0:
             src, co = _monomial_source(J)
@@ -557,7 +569,7 @@ def emit_pair_adjoint(lv: Level):
                     acc("g%d%s%d" % (mu, dn, K[d]), "D[%d]" % c2, mj)
     L.append(ind + "R ax = R(0), ay = R(0), az = R(0), radial = R(0);")
     for mu in range(lv.nmu):
-        nus = sorted({sum(K) for (m, K) in lv.comps if m == mu})
+        nus = sorted({sum(K) for (m, K) in comps if m == mu})
         if not nus:
             L.append(ind + "S[%d] = R(0);" % mu)
             continue
@@ -774,9 +786,58 @@ def emit_contract_program(lv: Level):
     L.append("    return interpret_contract<R, WANT_B, NCOMP, NVALUES, ONE, BOFF, NBASIS, NRECORDS>("
              "kProg%s, kStarts%s, M, xi, D, B);" % (nm, nm))
     L.append("  }")
+    L.append("  // V[0, NCOMP) = moments on entry, A[0, NCOMP) = dE/dM on return (arrays of NVALUES)")
+    L.append("  template <class R, bool WANT_B>")
+    L.append("  __device__ static R contract_values(R* V, R* A, const typename ScalarOf<R>::T* __restrict__ xi, "
+             "R* B) {")
+    L.append("    return interpret_values<R, WANT_B, NCOMP, NVALUES, ONE, BOFF, NBASIS, NRECORDS>("
+             "kProg%s, kStarts%s, V, A, xi, B);" % (nm, nm))
+    L.append("  }")
     tables = ["__device__ const int32_t kProg%s[] = {%s};" % (nm, ",".join(str(v) for v in prog)),
               "__device__ const int32_t kStarts%s[] = {%s};" % (nm, ",".join(str(v) for v in starts))]
     return L, tables
+
+
+def emit_groups(lv: Level):
+    """Per component group G: moments_group<G>, pair_adjoint_group<G> (the
+    group's terms only; S[mu] of other groups set to zero), store_group<G>
+    (group components of a register array into a full vector with stride
+    ld) and load_group<G>, plus the radial-function range [MU_LO, MU_HI)."""
+    L = []
+    ng = len(lv.groups)
+    for g, grp in enumerate(lv.groups):
+        sub = set(grp)
+        L += emit_moments(lv, sub, "moments_g%d" % g)
+        L += emit_pair_adjoint(lv, sub, "pair_adjoint_g%d" % g)
+        L.append("  template <class R>")
+        L.append("  __device__ __forceinline__ static void store_g%d(const R* __restrict__ Mg, R* __restrict__ M, "
+                 "int64_t ld) {" % g)
+        L += ["    M[%d * ld] = Mg[%d];" % (c, c) for c in grp]
+        L.append("  }")
+        L.append("  template <class R>")
+        L.append("  __device__ __forceinline__ static void load_g%d(const R* __restrict__ D, int64_t ld, "
+                 "R* __restrict__ Dg) {" % g)
+        L += ["    Dg[%d] = D[%d * ld];" % (c, c) for c in grp]
+        L.append("  }")
+    mus = [sorted({lv.comps[c][0] for c in grp}) for grp in lv.groups]
+    L.append("  static constexpr int GROUP_MU_LO[%d] = {%s};" % (ng, ", ".join(str(m[0]) for m in mus)))
+    L.append("  static constexpr int GROUP_MU_HI[%d] = {%s};" % (ng, ", ".join(str(m[-1] + 1) for m in mus)))
+    for fn, args, call in (
+            ("moments_group", "R* __restrict__ M, const R* __restrict__ f, R ux, R uy, R uz", "(M, f, ux, uy, uz)"),
+            ("pair_adjoint_group", "const R* __restrict__ D, const R* __restrict__ f, const R* __restrict__ df, "
+             "R ux, R uy, R uz, R rinv, R& gx, R& gy, R& gz, R* __restrict__ S",
+             "(D, f, df, ux, uy, uz, rinv, gx, gy, gz, S)"),
+            ("store_group", "const R* __restrict__ Mg, R* __restrict__ M, int64_t ld", "(Mg, M, ld)"),
+            ("load_group", "const R* __restrict__ D, int64_t ld, R* __restrict__ Dg", "(D, ld, Dg)")):
+        base = {"moments_group": "moments_g", "pair_adjoint_group": "pair_adjoint_g",
+                "store_group": "store_g", "load_group": "load_g"}[fn]
+        L.append("  template <int G, class R>")
+        L.append("  __device__ __forceinline__ static void %s(%s) {" % (fn, args))
+        for g in range(ng):
+            kw = "if" if g == 0 else "else if"
+            L.append("    %s constexpr (G == %d) %s%d<R>%s;" % (kw, g, base, g, call))
+        L.append("  }")
+    return L
 
 
 def emit_header(lv: Level):
@@ -794,8 +855,11 @@ def emit_header(lv: Level):
     out.append("  static constexpr int NBASIS = %d;" % lv.m)
     out.append("  static constexpr int NGRAPH = %d;" % len(lv.graphs))
     out.append("  static constexpr int NUMAX = %d;" % max(lv.nu_max))
+    out.append("  static constexpr int NGROUPS = %d;" % len(lv.groups))
     out += emit_moments(lv)
     out += emit_pair_adjoint(lv)
+    if len(lv.groups) > 1:
+        out += emit_groups(lv)
     if lv.level >= INTERPRET_FROM_LEVEL:
         body, tables = emit_contract_program(lv)
         out = out[:out.index("struct %s {" % name)] + tables + out[out.index("struct %s {" % name):]

@@ -73,15 +73,17 @@ def generate_sources(levels=LEVELS):
             "  return batch_launch<MtpLevel%d>(b, precision, want_dtheta, threads, s);\n}\n"
             "int tangent_level%d(const TangentArgs& t, int precision, cudaStream_t s) {\n"
             "  return tangent_launch<MtpLevel%d>(t, precision, s);\n}\n"
-            "}  // namespace mtp\n") % (L, L, L, L, L, L, L, L, L))
+            "int split_level%d() { return MtpLevel%d::NGROUPS > 1 ? MtpLevel%d::NCOMP : 0; }\n"
+            "}  // namespace mtp\n") % (L, L, L, L, L, L, L, L, L, L, L, L))
         units.append(path)
     decl = "".join("int efv_level%d(const EfvArgs&, int, bool, cudaStream_t);\n"
                    "int rows_level%d(const EfvArgs&, const int32_t*, int64_t, double*, int64_t, double*, cudaStream_t);\n"
                    "int batch_level%d(const BatchArgs&, int, bool, int, cudaStream_t);\n"
                    "int tangent_level%d(const TangentArgs&, int, cudaStream_t);\n"
-                   % (L, L, L, L) for L in levels)
-    table = ",\n".join("  {%d, efv_level%d, rows_level%d, batch_level%d, tangent_level%d, 0}" % (L, L, L, L, L)
-                        for L in levels)
+                   "int split_level%d();\n"
+                   % (L, L, L, L, L) for L in levels)
+    table = ",\n".join("  {%d, efv_level%d, rows_level%d, batch_level%d, tangent_level%d, split_level%d()}"
+                        % (L, L, L, L, L, L) for L in levels)
     reg = os.path.join(GEN, "levels.cu")
     _write(reg, (
         "// Generated by paper_2510_00193_gb300/build.py.\n#include \"mtp_internal.cuh\"\nnamespace mtp {\n%s"

@@ -294,26 +294,12 @@ struct EfvShared {
   }
 };
 
-// Everything one centre atom contributes: its site energy (also stored in
-// e_atom), its force terms (scattered), its virial terms (w) and, with
-// DTHETA, its basis values and radial-coefficient gradient (shared
-// accumulators).  `cell` holds the rows of its configuration's cell.
-// Every lane of the warp calls this (the basis values are summed across the
-// warp right after the contraction, which frees their registers for the
-// second sweep): a lane without an atom passes active = false and a valid
-// atom index i, runs no pairs, writes nothing and contributes zeros (every
-// basis function vanishes at zero moments).
-template <class LV, class R, bool DTHETA>
-__device__ __forceinline__ void efv_atom(const EfvArgs& a, const EfvShared<R, LV::NMU, DTHETA>& sm, int64_t i,
-                                         bool active, const R* cell, double& e_i, R* w) {
+// First neighbour sweep: M[c] += f_mu(r_ij) rhat^K for the components of
+// group G (G < 0: all components; G >= 0: the level's component group G).
+template <class LV, class R, bool DTHETA, int G>
+__device__ __forceinline__ void moment_sweep(const EfvArgs& a, const EfvShared<R, LV::NMU, DTHETA>& sm,
+                                             const PairGeom<R>& geom, int zi, int64_t beg, int64_t end, R* M) {
   constexpr int NMU = LV::NMU;
-  PairGeom<R> geom;
-  geom.load_centre(a, i, cell);
-  const int zi = __ldg(a.z + i);
-  const int64_t beg = active ? __ldg(a.offsets + i) : 0, end = active ? __ldg(a.offsets + i + 1) : 0;
-  R M[LV::NCOMP];
-#pragma unroll
-  for (int c = 0; c < LV::NCOMP; ++c) M[c] = R(0);
   PairStream<R> ps;
   int32_t j, img;
   typename PairGeom<R>::Load lj;
@@ -327,7 +313,117 @@ __device__ __forceinline__ void efv_atom(const EfvArgs& a, const EfvShared<R, LV
     R f[NMU];
     radial<R, NMU, false, false>(sm.c + (zi * sm.S + lj.species) * sm.cstride, sm.nq, r, sm.mid, sm.scale, sm.rcut, f,
                                  nullptr, nullptr);
-    LV::template moments<R>(M, f, dx * rinv, dy * rinv, dz * rinv);
+    if constexpr (G < 0) LV::template moments<R>(M, f, dx * rinv, dy * rinv, dz * rinv);
+    else LV::template moments_group<G, R>(M, f, dx * rinv, dy * rinv, dz * rinv);
+  }
+}
+
+// Second neighbour sweep for the components of group G (G < 0: all): per pair
+// g_ij = dE_i/dr_ij from D (the group's share), F_i += g, F_j -= g,
+// W -= sym(g (x) r_ij) and, with DTHETA, the group's radial functions'
+// dE/dc terms Q_k(r) S_mu into acc (own_acc) or the shared accumulators.
+template <class LV, class R, bool DTHETA, int G>
+__device__ __forceinline__ void adjoint_sweep(const EfvArgs& a, const EfvShared<R, LV::NMU, DTHETA>& sm,
+                                              const PairGeom<R>& geom, int zi, int64_t beg, int64_t end,
+                                              const R* D, R& fx, R& fy, R& fz, R* w, R* acc, bool own_acc) {
+  constexpr int NMU = LV::NMU;
+  PairStream<R> ps;
+  int32_t j, img;
+  typename PairGeom<R>::Load lj;
+  ps.start(a, geom, beg, end);
+  while (ps.next(a, geom, j, img, lj)) {
+    const int zj = lj.species;
+    R dx, dy, dz;
+    geom.vec(a, lj, img, dx, dy, dz);
+    const R r2 = fmadd(dz, dz, fmadd(dy, dy, dx * dx));
+    const R rinv = rsqrt_r(r2);
+    const R r = r2 * rinv;
+    R f[NMU], df[NMU], q[DTHETA ? kMaxQ : 1];
+    radial<R, NMU, true, DTHETA>(sm.c + (zi * sm.S + zj) * sm.cstride, sm.nq, r, sm.mid, sm.scale, sm.rcut, f, df, q);
+    R gx, gy, gz, Smu[NMU];
+    if constexpr (G < 0)
+      LV::template pair_adjoint<R>(D, f, df, dx * rinv, dy * rinv, dz * rinv, rinv, gx, gy, gz, Smu);
+    else
+      LV::template pair_adjoint_group<G, R>(D, f, df, dx * rinv, dy * rinv, dz * rinv, rinv, gx, gy, gz, Smu);
+    fx += gx; fy += gy; fz += gz;
+    scatter_force(a, j, -gx, -gy, -gz);
+    w[0] = fmadd(-gx, dx, w[0]);
+    w[1] = fmadd(-gy, dy, w[1]);
+    w[2] = fmadd(-gz, dz, w[2]);
+    w[3] = fmadd(R(-0.5), fmadd(gx, dy, gy * dx), w[3]);
+    w[4] = fmadd(R(-0.5), fmadd(gx, dz, gz * dx), w[4]);
+    w[5] = fmadd(R(-0.5), fmadd(gy, dz, gz * dy), w[5]);
+    if (DTHETA) {
+      int mu_lo = 0, mu_hi = NMU;
+      if constexpr (G >= 0) {
+        mu_lo = LV::GROUP_MU_LO[G];
+        mu_hi = LV::GROUP_MU_HI[G];
+      }
+      if (own_acc) {
+        R* dst = acc + zj * NMU * sm.nq;
+#pragma unroll
+        for (int mu = 0; mu < NMU; ++mu) {
+          if (mu < mu_lo || mu >= mu_hi) continue;
+#pragma unroll
+          for (int kk = 0; kk < kMaxQ; ++kk)
+            if (kk < sm.nq) dst[mu * sm.nq + kk] = fmadd(q[kk], Smu[mu], dst[mu * sm.nq + kk]);
+        }
+      } else {
+        R* dst = sm.dc + (zi * sm.S + zj) * NMU * sm.nq;
+#pragma unroll
+        for (int mu = 0; mu < NMU; ++mu) {
+          if (mu < mu_lo || mu >= mu_hi) continue;
+#pragma unroll
+          for (int kk = 0; kk < kMaxQ; ++kk)
+            if (kk < sm.nq) atomicAdd(dst + mu * sm.nq + kk, q[kk] * Smu[mu]);
+        }
+      }
+    }
+  }
+}
+
+// Everything one centre atom contributes: its site energy (also stored in
+// e_atom), its force terms (scattered), its virial terms (w) and, with
+// DTHETA, its basis values and radial-coefficient gradient (shared
+// accumulators).  `cell` holds the rows of its configuration's cell.
+// Every lane of the warp calls this (the basis values are summed across the
+// warp right after the contraction, which frees their registers for the
+// second sweep): a lane without an atom passes active = false and a valid
+// atom index i, runs no pairs, writes nothing and contributes zeros (every
+// basis function vanishes at zero moments).
+// Levels with component groups (the interpreted contractions of levels 18
+// and 20: 201 and 295 components) sweep the neighbours once per group, so
+// that a group's moments, then its adjoints, stay in registers; the full
+// vectors meet the interpreter once per atom.
+template <class LV, class R, bool DTHETA>
+__device__ __forceinline__ void efv_atom(const EfvArgs& a, const EfvShared<R, LV::NMU, DTHETA>& sm, int64_t i,
+                                         bool active, const R* cell, double& e_i, R* w) {
+  constexpr int NMU = LV::NMU;
+  static_assert(LV::NGROUPS == 1 || LV::NGROUPS == 2, "one or two component groups");
+  PairGeom<R> geom;
+  geom.load_centre(a, i, cell);
+  const int zi = __ldg(a.z + i);
+  const int64_t beg = active ? __ldg(a.offsets + i) : 0, end = active ? __ldg(a.offsets + i + 1) : 0;
+  R M[LV::NCOMP];
+#pragma unroll
+  for (int c = 0; c < LV::NCOMP; ++c) M[c] = R(0);
+  if constexpr (LV::NGROUPS == 1) {
+    moment_sweep<LV, R, DTHETA, -1>(a, sm, geom, zi, beg, end, M);
+  } else {
+    {
+      R Mg[LV::NCOMP];
+#pragma unroll
+      for (int c = 0; c < LV::NCOMP; ++c) Mg[c] = R(0);
+      moment_sweep<LV, R, DTHETA, 0>(a, sm, geom, zi, beg, end, Mg);
+      LV::template store_group<0, R>(Mg, M, 1);
+    }
+    {
+      R Mg[LV::NCOMP];
+#pragma unroll
+      for (int c = 0; c < LV::NCOMP; ++c) Mg[c] = R(0);
+      moment_sweep<LV, R, DTHETA, 1>(a, sm, geom, zi, beg, end, Mg);
+      LV::template store_group<1, R>(Mg, M, 1);
+    }
   }
   R D[LV::NCOMP];
   R Bv[DTHETA ? LV::NBASIS : 1];
@@ -357,44 +453,18 @@ __device__ __forceinline__ void efv_atom(const EfvArgs& a, const EfvShared<R, LV
   if (own_acc) {
     for (int t = 0; t < sm.S * NMU * sm.nq; ++t) acc[t] = R(0);
   }
-  ps.start(a, geom, beg, end);
-  while (ps.next(a, geom, j, img, lj)) {
-    const int zj = lj.species;
-    R dx, dy, dz;
-    geom.vec(a, lj, img, dx, dy, dz);
-    const R r2 = fmadd(dz, dz, fmadd(dy, dy, dx * dx));
-    const R rinv = rsqrt_r(r2);
-    const R r = r2 * rinv;
-    R f[NMU], df[NMU], q[DTHETA ? kMaxQ : 1];
-    radial<R, NMU, true, DTHETA>(sm.c + (zi * sm.S + zj) * sm.cstride, sm.nq, r, sm.mid, sm.scale, sm.rcut, f, df, q);
-    R gx, gy, gz, Smu[NMU];
-    LV::template pair_adjoint<R>(D, f, df, dx * rinv, dy * rinv, dz * rinv, rinv, gx, gy, gz, Smu);
-    fx += gx; fy += gy; fz += gz;
-    scatter_force(a, j, -gx, -gy, -gz);
-    w[0] = fmadd(-gx, dx, w[0]);
-    w[1] = fmadd(-gy, dy, w[1]);
-    w[2] = fmadd(-gz, dz, w[2]);
-    w[3] = fmadd(R(-0.5), fmadd(gx, dy, gy * dx), w[3]);
-    w[4] = fmadd(R(-0.5), fmadd(gx, dz, gz * dx), w[4]);
-    w[5] = fmadd(R(-0.5), fmadd(gy, dz, gz * dy), w[5]);
-    if (DTHETA) {
-      if (own_acc) {
-        R* dst = acc + zj * NMU * sm.nq;
-#pragma unroll
-        for (int mu = 0; mu < NMU; ++mu) {
-#pragma unroll
-          for (int kk = 0; kk < kMaxQ; ++kk)
-            if (kk < sm.nq) dst[mu * sm.nq + kk] = fmadd(q[kk], Smu[mu], dst[mu * sm.nq + kk]);
-        }
-      } else {
-        R* dst = sm.dc + (zi * sm.S + zj) * NMU * sm.nq;
-#pragma unroll
-        for (int mu = 0; mu < NMU; ++mu) {
-#pragma unroll
-          for (int kk = 0; kk < kMaxQ; ++kk)
-            if (kk < sm.nq) atomicAdd(dst + mu * sm.nq + kk, q[kk] * Smu[mu]);
-        }
-      }
+  if constexpr (LV::NGROUPS == 1) {
+    adjoint_sweep<LV, R, DTHETA, -1>(a, sm, geom, zi, beg, end, D, fx, fy, fz, w, acc, own_acc);
+  } else {
+    {
+      R Dg[LV::NCOMP];
+      LV::template load_group<0, R>(D, 1, Dg);
+      adjoint_sweep<LV, R, DTHETA, 0>(a, sm, geom, zi, beg, end, Dg, fx, fy, fz, w, acc, own_acc);
+    }
+    {
+      R Dg[LV::NCOMP];
+      LV::template load_group<1, R>(D, 1, Dg);
+      adjoint_sweep<LV, R, DTHETA, 1>(a, sm, geom, zi, beg, end, Dg, fx, fy, fz, w, acc, own_acc);
     }
   }
   if (!active) return;
@@ -413,9 +483,12 @@ __device__ __forceinline__ void efv_atom(const EfvArgs& a, const EfvShared<R, LV
 // Block-wide FP64 reduction of the block's energy, virial and gradient into
 // e_out[0], w_out[0..6) and theta_out (layout [ s | c[mu][k][zi][zj] | xi ]).
 // Must be reached by every thread of the block.
+constexpr unsigned kFlushEW = 1, kFlushDc = 2, kFlushDxi = 4, kFlushAll = 7;
+
 template <class LV, class R, bool DTHETA>
 __device__ __forceinline__ void efv_block_flush(const EfvShared<R, LV::NMU, DTHETA>& sm, double e_i, const R* w,
-                                                double* e_out, double* w_out, double* theta_out) {
+                                                double* e_out, double* w_out, double* theta_out,
+                                                unsigned parts = kFlushAll) {
   constexpr int NMU = LV::NMU;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int nwarps = (blockDim.x + 31) >> 5;
@@ -427,7 +500,7 @@ __device__ __forceinline__ void efv_block_flush(const EfvShared<R, LV::NMU, DTHE
     for (int t = 0; t < 7; ++t) sm.red[warp * 8 + t] = vals[t];
   }
   __syncthreads();
-  if (threadIdx.x < 7) {
+  if ((parts & kFlushEW) && threadIdx.x < 7) {
     double acc = 0.0;
     for (int wi = 0; wi < nwarps; ++wi) acc += sm.red[wi * 8 + threadIdx.x];
     if (threadIdx.x == 0) atomicAdd(e_out, acc);
@@ -435,14 +508,18 @@ __device__ __forceinline__ void efv_block_flush(const EfvShared<R, LV::NMU, DTHE
   }
   if (DTHETA) {
     const int S = sm.S, SS = sm.SS, nq = sm.nq;
-    for (int t = threadIdx.x; t < S; t += blockDim.x) atomicAdd(theta_out + t, (double)sm.cnt[t]);
-    for (int t = threadIdx.x; t < SS * NMU * nq; t += blockDim.x) {
-      const int p = t / (NMU * nq);
-      const int mk = t % (NMU * nq);
-      atomicAdd(theta_out + S + (int64_t)mk * SS + p, (double)sm.dc[t]);
+    if (parts & kFlushDxi)
+      for (int t = threadIdx.x; t < S; t += blockDim.x) atomicAdd(theta_out + t, (double)sm.cnt[t]);
+    if (parts & kFlushDc) {
+      for (int t = threadIdx.x; t < SS * NMU * nq; t += blockDim.x) {
+        const int p = t / (NMU * nq);
+        const int mk = t % (NMU * nq);
+        atomicAdd(theta_out + S + (int64_t)mk * SS + p, (double)sm.dc[t]);
+      }
     }
-    for (int t = threadIdx.x; t < sm.m; t += blockDim.x)
-      atomicAdd(theta_out + S + (int64_t)NMU * nq * SS + t, (double)sm.dxi[t]);
+    if (parts & kFlushDxi)
+      for (int t = threadIdx.x; t < sm.m; t += blockDim.x)
+        atomicAdd(theta_out + S + (int64_t)NMU * nq * SS + t, (double)sm.dxi[t]);
   }
 }
 
@@ -462,8 +539,176 @@ __global__ void __launch_bounds__(kEfvThreads) efv_kernel(const EfvArgs a) {
   efv_block_flush<LV, R, DTHETA>(sm, e_i, w, a.e_total, a.virial, a.dtheta);
 }
 
+// Levels with component groups (interpreted contraction) and a scratch
+// buffer a.mbuf run as three kernels: the interpreter's per-thread value
+// arrays stream through local memory, which needs many resident warps, while
+// the neighbour sweeps need many registers per thread.  a.mbuf holds the
+// moment vectors of the atom range and then their adjoints, component-major:
+// [2][c][atom - atom_begin].
+template <class LV, class R>
+__global__ void __launch_bounds__(kEfvThreads) split_moments_kernel(const EfvArgs a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  EfvShared<R, LV::NMU, false> sm;
+  sm.setup(a, smem_raw);
+  __syncthreads();
+  const int64_t n = a.atom_end - a.atom_begin;
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const bool active = t < n;
+  if (!__any_sync(0xffffffffu, active)) return;
+  const int64_t i = a.atom_begin + (active ? t : 0);
+  PairGeom<R> geom;
+  geom.load_centre(a, i, cell_of<R>(a));
+  const int zi = __ldg(a.z + i);
+  const int64_t beg = active ? __ldg(a.offsets + i) : 0, end = active ? __ldg(a.offsets + i + 1) : 0;
+  R* buf = static_cast<R*>(a.mbuf) + (active ? t : 0);
+  {
+    R Mg[LV::NCOMP];
+#pragma unroll
+    for (int c = 0; c < LV::NCOMP; ++c) Mg[c] = R(0);
+    moment_sweep<LV, R, false, 0>(a, sm, geom, zi, beg, end, Mg);
+    if (active) LV::template store_group<0, R>(Mg, buf, n);
+  }
+  {
+    R Mg[LV::NCOMP];
+#pragma unroll
+    for (int c = 0; c < LV::NCOMP; ++c) Mg[c] = R(0);
+    moment_sweep<LV, R, false, 1>(a, sm, geom, zi, beg, end, Mg);
+    if (active) LV::template store_group<1, R>(Mg, buf, n);
+  }
+}
+
+template <class LV, class R, bool DTHETA>
+__global__ void __launch_bounds__(kEfvThreads) split_contract_kernel(const EfvArgs a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  EfvShared<R, LV::NMU, DTHETA> sm;
+  sm.setup(a, smem_raw);
+  sm.zero_gradients();
+  __syncthreads();
+  const int64_t n = a.atom_end - a.atom_begin;
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const bool active = t < n;
+  double e_i = 0.0;
+  const R w[6] = {R(0), R(0), R(0), R(0), R(0), R(0)};
+  if (__any_sync(0xffffffffu, active)) {
+    const R* __restrict__ mrow = static_cast<const R*>(a.mbuf) + (active ? t : 0);
+    R* __restrict__ drow = static_cast<R*>(a.mbuf) + (size_t)LV::NCOMP * n + (active ? t : 0);
+    R V[LV::NVALUES], A[LV::NVALUES];
+    R Bv[DTHETA ? LV::NBASIS : 1];
+    for (int c = 0; c < LV::NCOMP; ++c) V[c] = active ? mrow[c * n] : R(0);
+    const R ei = LV::template contract_values<R, DTHETA>(V, A, sm.xi, Bv);
+    if (active)
+      for (int c = 0; c < LV::NCOMP; ++c) drow[c * n] = A[c];
+    if (DTHETA) {
+      const int lane = threadIdx.x & 31;
+#pragma unroll
+      for (int u = 0; u < (DTHETA ? LV::NBASIS : 1); ++u) {
+        const R v = warp_sum_r(active ? Bv[u] : R(0));
+        if (lane == 0) atomicAdd(sm.dxi + u, v);
+      }
+    }
+    if (active) {
+      const int64_t i = a.atom_begin + t;
+      const int zi = __ldg(a.z + i);
+      e_i = a.species_energy[zi] + (double)ei;
+      a.e_atom[i] = e_i;
+      if (!isfinite(e_i)) flag_status(a.status, MTP_ERR_NONFINITE);
+      if (DTHETA) atomicAdd(sm.cnt + zi, 1);
+    }
+  }
+  efv_block_flush<LV, R, DTHETA>(sm, e_i, w, a.e_total, a.virial, a.dtheta, kFlushEW | kFlushDxi);
+}
+
+template <class LV, class R, bool DTHETA>
+__global__ void __launch_bounds__(kEfvThreads) split_adjoint_kernel(const EfvArgs a) {
+  constexpr int NMU = LV::NMU;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  EfvShared<R, NMU, DTHETA> sm;
+  sm.setup(a, smem_raw);
+  sm.zero_gradients();
+  __syncthreads();
+  const int64_t n = a.atom_end - a.atom_begin;
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const bool active = t < n;
+  R w[6] = {R(0), R(0), R(0), R(0), R(0), R(0)};
+  if (__any_sync(0xffffffffu, active)) {
+    const int64_t i = a.atom_begin + (active ? t : 0);
+    PairGeom<R> geom;
+    geom.load_centre(a, i, cell_of<R>(a));
+    const int zi = __ldg(a.z + i);
+    const int64_t beg = active ? __ldg(a.offsets + i) : 0, end = active ? __ldg(a.offsets + i + 1) : 0;
+    const R* buf = static_cast<const R*>(a.mbuf) + (size_t)LV::NCOMP * n + (active ? t : 0);
+    R fx = R(0), fy = R(0), fz = R(0);
+    constexpr int kAccS = 4;
+    const bool own_acc = DTHETA && sm.S <= kAccS;
+    R acc[DTHETA ? kAccS * NMU * kMaxQ : 1];
+    if (own_acc) {
+      for (int u = 0; u < sm.S * NMU * sm.nq; ++u) acc[u] = R(0);
+    }
+    {
+      R Dg[LV::NCOMP];
+      LV::template load_group<0, R>(buf, n, Dg);
+      adjoint_sweep<LV, R, DTHETA, 0>(a, sm, geom, zi, beg, end, Dg, fx, fy, fz, w, acc, own_acc);
+    }
+    {
+      R Dg[LV::NCOMP];
+      LV::template load_group<1, R>(buf, n, Dg);
+      adjoint_sweep<LV, R, DTHETA, 1>(a, sm, geom, zi, beg, end, Dg, fx, fy, fz, w, acc, own_acc);
+    }
+    if (active) {
+      if (own_acc) {
+        for (int zj = 0; zj < sm.S; ++zj) {
+          R* dst = sm.dc + (zi * sm.S + zj) * NMU * sm.nq;
+          for (int u = 0; u < NMU * sm.nq; ++u) atomicAdd(dst + u, acc[zj * NMU * sm.nq + u]);
+        }
+      }
+      scatter_force(a, i, fx, fy, fz);
+      if (!isfinite((double)fx) || !isfinite((double)fy) || !isfinite((double)fz))
+        flag_status(a.status, MTP_ERR_NONFINITE);
+    }
+  }
+  efv_block_flush<LV, R, DTHETA>(sm, 0.0, w, a.e_total, a.virial, a.dtheta, kFlushEW | kFlushDc);
+}
+
+template <class K>
+int set_smem(K kern, size_t bytes) {
+  if (bytes > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    if (e != cudaSuccess) {
+      set_error("cudaFuncSetAttribute: %s", cudaGetErrorString(e));
+      return MTP_ERR_CUDA;
+    }
+  }
+  return MTP_OK;
+}
+
+template <class LV, class R, bool DTHETA>
+int efv_split_launch(const EfvArgs& a, cudaStream_t stream) {
+  const int SS = a.n_species * a.n_species;
+  const int64_t n = a.atom_end - a.atom_begin;
+  if (n <= 0) return MTP_OK;
+  const unsigned grid = (unsigned)((n + kEfvThreads - 1) / kEfvThreads);
+  const size_t b0 = efv_smem_bytes<R, LV::NMU, false>(SS, a.n_q, a.m);
+  const size_t b1 = efv_smem_bytes<R, LV::NMU, DTHETA>(SS, a.n_q, a.m);
+  int rc;
+  if ((rc = set_smem(split_moments_kernel<LV, R>, b0)) != MTP_OK) return rc;
+  if ((rc = set_smem(split_contract_kernel<LV, R, DTHETA>, b1)) != MTP_OK) return rc;
+  if ((rc = set_smem(split_adjoint_kernel<LV, R, DTHETA>, b1)) != MTP_OK) return rc;
+  split_moments_kernel<LV, R><<<grid, kEfvThreads, b0, stream>>>(a);
+  split_contract_kernel<LV, R, DTHETA><<<grid, kEfvThreads, b1, stream>>>(a);
+  split_adjoint_kernel<LV, R, DTHETA><<<grid, kEfvThreads, b1, stream>>>(a);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) {
+    set_error("efv split kernels (level %d): %s", LV::LEVEL, cudaGetErrorString(e));
+    return MTP_ERR_CUDA;
+  }
+  return MTP_OK;
+}
+
 template <class LV, class R, bool DTHETA>
 int efv_launch_typed(const EfvArgs& a, cudaStream_t stream) {
+  if constexpr (LV::NGROUPS > 1) {
+    if (a.mbuf) return efv_split_launch<LV, R, DTHETA>(a, stream);
+  }
   const int SS = a.n_species * a.n_species;
   const size_t bytes = efv_smem_bytes<R, LV::NMU, DTHETA>(SS, a.n_q, a.m);
   auto kern = efv_kernel<LV, R, DTHETA>;

@@ -232,6 +232,7 @@ void mtp_free(mtp_handle* h) {
   h->xq.release();
   h->forces_f.release();
   h->grade.release();
+  h->mbuf.release();
   delete h;
 }
 
@@ -421,6 +422,15 @@ int mtp_compute_efv(mtp_handle* h, const mtp_nlist* nl, const double* x, const i
     MTP_TRY_CUDA(cudaGetLastError());
   }
   const int64_t chunk = chunk_atoms > 0 ? chunk_atoms : n;
+  if (h->ops->split_comps > 0 && n > 0) {
+    // moment/adjoint scratch of the split kernels (levels with an interpreted
+    // contraction), bounded by the chunk as the paper's chunk size bounds memory
+    const size_t bytes = 2 * (size_t)h->ops->split_comps * (size_t)std::min<int64_t>(chunk, n) *
+                         (precision == MTP_MIXED ? sizeof(float) : sizeof(double));
+    int rc = h->mbuf.ensure(bytes);
+    if (rc != MTP_OK) return rc;
+    a.mbuf = h->mbuf.ptr;
+  }
   for (int64_t b = 0; b < n; b += chunk) {
     a.atom_begin = b;
     a.atom_end = b + chunk < n ? b + chunk : n;

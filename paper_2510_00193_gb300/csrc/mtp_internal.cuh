@@ -70,6 +70,8 @@ struct EfvArgs {
   double* e_total;
   double* dtheta;           // nullable
   int* status;
+  void* mbuf;               // levels with component groups: moment and adjoint scratch
+                            // [2][NCOMP][atom_end - atom_begin] in the working precision (nullptr: one fused kernel)
 };
 
 using EfvLaunch = int (*)(const EfvArgs&, int precision, bool want_dtheta, cudaStream_t);
@@ -88,7 +90,7 @@ struct LevelEntry {
   RowsLaunch rows;
   BatchLaunch batch;
   TangentLaunch tangent;
-  int shmem_bytes_max;
+  int split_comps;   // components per atom of the EfvArgs::mbuf scratch (0: the level needs none)
 };
 
 const LevelEntry* find_level(int level);
@@ -120,6 +122,7 @@ struct mtp_handle {
   mtp::DevBuf xq;        // fixed-point positions scratch
   mtp::DevBuf forces_f;  // FP32 force accumulator (mixed path)
   mtp::DevBuf grade;     // grade scratch: counters, row maxima, column sums, FP64 basis rows
+  mtp::DevBuf mbuf;      // moment/adjoint scratch of levels whose contraction is interpreted
 };
 
 struct mtp_nlist {

@@ -10,14 +10,11 @@
 
 namespace mtp {
 
+// Core: V[0, NCOMP) holds the moment components on entry; on return A[0,
+// NCOMP) holds D = dE/dM.  V and A are caller arrays of NV values.
 template <class R, bool WANT_B, int NCOMP, int NV, int ONE, int BOFF, int NB, int NREC>
-__device__ __forceinline__ R interpret_contract(const int32_t* __restrict__ prog, const int32_t* __restrict__ starts,
-                                                const R* __restrict__ M,
-                                                const typename ScalarOf<R>::T* __restrict__ xi, R* __restrict__ D,
-                                                R* __restrict__ B) {
-  R V[NV];
-  R A[NV];
-  for (int c = 0; c < NCOMP; ++c) V[c] = M[c];
+__device__ __forceinline__ R interpret_values(const int32_t* __restrict__ prog, const int32_t* __restrict__ starts,
+                                              R* V, R* A, const typename ScalarOf<R>::T* __restrict__ xi, R* B) {
   V[ONE] = R(1);
   for (int r = 0; r < NREC; ++r) {
     const int32_t* p = prog + starts[r];
@@ -62,6 +59,18 @@ __device__ __forceinline__ R interpret_contract(const int32_t* __restrict__ prog
       }
     }
   }
+  return E;
+}
+
+template <class R, bool WANT_B, int NCOMP, int NV, int ONE, int BOFF, int NB, int NREC>
+__device__ __forceinline__ R interpret_contract(const int32_t* __restrict__ prog, const int32_t* __restrict__ starts,
+                                                const R* __restrict__ M,
+                                                const typename ScalarOf<R>::T* __restrict__ xi, R* __restrict__ D,
+                                                R* __restrict__ B) {
+  R V[NV];
+  R A[NV];
+  for (int c = 0; c < NCOMP; ++c) V[c] = M[c];
+  const R E = interpret_values<R, WANT_B, NCOMP, NV, ONE, BOFF, NB, NREC>(prog, starts, V, A, xi, B);
   for (int c = 0; c < NCOMP; ++c) D[c] = A[c];
   return E;
 }
