@@ -550,5 +550,13 @@ extern "C" int mtp_compute_efv_tangent(mtp_handle* h, const mtp_nlist* nl, const
   }
   t.base.atom_begin = 0;
   t.base.atom_end = n;
+  if (h->ops->split_comps > 0 && n > 0) {
+    // dual moments and adjoints of the split tangent kernels: 2 x components x atoms (value, tangent) pairs
+    const size_t bytes = 4 * (size_t)h->ops->split_comps * (size_t)n *
+                         (precision == MTP_MIXED ? sizeof(float) : sizeof(double));
+    int rc = h->mbuf.ensure(bytes);
+    if (rc != MTP_OK) return rc;
+    t.base.mbuf = h->mbuf.ptr;
+  }
   return h->ops->tangent(t, precision, s);
 }

@@ -173,6 +173,29 @@ def test_chunked_launches_match_single_launch(P):
     assert np.abs(a["forces"] - b["forces"]).max() <= 1e-12
 
 
+def test_level20_split_kernels_in_chunks_match_oracle(P):
+    """Level 20 runs as three kernels (moment sweep, contraction, adjoint
+    sweep) through a scratch of the chunk's moments: 108-atom FCC (4 species)
+    in one chunk, in chunks of 37 (a ragged last chunk) and of one atom, FP64
+    with dE/dtheta against the oracle; mixed chunked against unchunked."""
+    name = "fcc-l20-s4"
+    st = structure("fcc", (3, 3, 3), 3.6, 0.1, 4, 3)
+    model = oracle_model(name)
+    nl = O.neighbor_list(st.x, st.cell, st.pbc, pot_dict(name)["r_cut"])
+    ref = O.evaluate(model, st.x, st.z, st.cell, nl, want=("e", "f", "w", "dtheta"))
+    theta_ref = np.concatenate([ref["dE_ds"], ref["dE_dc"].ravel(), ref["dE_dxi"]])
+    for chunk in (0, 37, 1):
+        got = run_gpu(P, name, st, P.MTP_FP64, dtheta=True, chunk=chunk)
+        assert np.all(np.abs(got["e_atom"] - ref["e_atom"]) <= 1e-12 * np.maximum(1.0, np.abs(ref["e_atom"]))), chunk
+        assert np.abs(got["forces"] - ref["f"]).max() <= 1e-10, chunk
+        assert np.abs(got["virial"] - ref["w"]).max() <= max(1e-10, 1e-10 * np.abs(ref["w"]).max()), chunk
+        assert np.all(np.abs(got["dtheta"] - theta_ref) <= 1e-10 * np.maximum(1.0, np.abs(theta_ref))), chunk
+    a = run_gpu(P, name, st, P.MTP_MIXED, dtheta=True)
+    b = run_gpu(P, name, st, P.MTP_MIXED, dtheta=True, chunk=37)
+    assert np.abs(a["e_atom"] - b["e_atom"]).max() <= 1e-9
+    assert np.abs(a["forces"] - b["forces"]).max() <= 1e-5
+
+
 def test_empty_and_isolated_atoms(P):
     pot = gpu_pot(P, "bcc-l8-s1")
     st = synth.Structure(np.array([[1.0, 1.0, 1.0], [30.0, 30.0, 30.0]]), np.zeros(2, np.int32), np.eye(3) * 60.0,
