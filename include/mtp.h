@@ -54,7 +54,8 @@ typedef enum {
   MTP_ERR_NEIGHBOR_OVERFLOW = -4,  /* a neighbour image lies beyond +-511 cells */
   MTP_ERR_NONFINITE = -5,          /* NaN/Inf in inputs or results */
   MTP_ERR_TIMEOUT = -6,            /* a device-side wait gave up */
-  MTP_ERR_UNSUPPORTED = -7         /* level not compiled into this library */
+  MTP_ERR_UNSUPPORTED = -7,        /* level not compiled into this library */
+  MTP_ERR_STALE_LIST = -8          /* MD: an atom moved more than skin/2 since the list build */
 } mtp_status;
 
 typedef enum { MTP_FP64 = 0, MTP_MIXED = 1 } mtp_precision;
@@ -240,6 +241,62 @@ void mtp_batch_free(mtp_batch* b);
 int mtp_compute_efv_noalloc(mtp_handle* h, const mtp_nlist* nl, const double* x_dev, const int32_t* z_dev,
                             int64_t n_atoms, const double* cell, int64_t chunk_atoms, double* e_atom_dev,
                             double* forces_dev, double* virial_dev, double* e_total_dev, void* stream);
+
+/* On-device molecular dynamics: velocity-Verlet (NVE) steps with the MTP
+ * forces.  The paper measures the potential inside LAMMPS molecular dynamics
+ * (100 steps of 1 fs per run, atom-timesteps per second: Sec. 2.2, Fig. 3;
+ * 1 fs MD in the examples of Sec. 3), with the neighbour list the MD engine
+ * hands to the pair style (Sec. 2.3).  One step is
+ *   v += (dt/2) F/m,  x += dt v,  F = -dE/dx at the new x,  v += (dt/2) F/m.
+ * Units: LAMMPS metal (x in A, v in A/ps, dt in ps, masses in amu, energies in
+ * eV; 1 amu A^2/ps^2 = 1.0364269e-4 eV).
+ * Neighbours: a skin list of every pair within R_cut + skin of the positions at
+ * its last build; every step it is filtered to the exact R_cut list of the
+ * current positions with the FP64 decision of mtp_build_neighbors (same
+ * entries in the same order as a fresh build, as long as no atom has moved more
+ * than skin/2 since the skin list was built).  Positions are never wrapped, so
+ * the image vectors of the skin list stay valid between builds.
+ *
+ * mtp_md_create: builds the skin list of x_dev [N][3] (DEVICE) in the cell
+ * (host [9]) with pbc (host [3]) and the exact list; the cell is fixed for
+ * the life of the object.  Synchronises `stream`.  Free with mtp_md_free. */
+typedef struct mtp_md mtp_md;
+int mtp_md_create(mtp_handle* h, const double* x_dev, int64_t n_atoms, const double* cell, const int32_t* pbc,
+                  double skin, mtp_md** out, void* stream);
+/* Rebuilds the skin list (and the exact list) at the positions x_dev.
+ * Synchronises `stream`. */
+int mtp_md_rebuild(mtp_handle* h, mtp_md* md, const double* x_dev, void* stream);
+/* The exact neighbour list of the current positions (owned by md, valid until
+ * the next call on md); usable with mtp_compute_efv, mtp_compute_grade and
+ * mtp_nlist_copy.  Synchronises `stream` (it reads the pair count). */
+int mtp_md_nlist(mtp_md* md, const mtp_nlist** nl, void* stream);
+/* MTP_ERR_STALE_LIST if an atom has moved more than skin/2 from its position
+ * at the last skin-list build (the exact lists since then may miss pairs),
+ * else MTP_OK; *steps_since_build (HOST, nullable) counts the steps run on the
+ * current skin list, *rebuilds (HOST, nullable) the skin-list builds since
+ * creation (the first included).  Synchronises `stream`. */
+int mtp_md_status(mtp_md* md, int64_t* steps_since_build, int64_t* rebuilds, void* stream);
+/* Runs n_steps velocity-Verlet steps in place on x_dev and v_dev ([N][3]
+ * DEVICE, FP64).  forces_dev [N][3] (DEVICE) holds on entry the forces at
+ * x_dev (from mtp_compute_efv on the exact list, or from the previous
+ * mtp_md_run) and on return the forces at the final positions.  mass: HOST
+ * [S] in amu.  precision: MTP_FP64 or MTP_MIXED for the forces (the
+ * integration itself is FP64).  e_pot_dev / e_kin_dev: DEVICE [n_steps]
+ * (nullable), the potential and kinetic energy after each step.
+ * rebuild_every < 0: after each drift the displacement check is read (one
+ * synchronisation per step) and the skin list is rebuilt at once when an atom
+ * has moved more than skin/2, so no step uses an incomplete list (the LAMMPS
+ * default of checking every step).
+ * rebuild_every > 0: the skin list is rebuilt after every rebuild_every steps
+ * (the displacement check is read before each rebuild and at the end, which
+ * synchronises; MTP_ERR_STALE_LIST stops the run).  rebuild_every = 0: no
+ * rebuild and no synchronisation (the call only queues work, so it can be
+ * captured in a CUDA graph once a first call has sized the scratch); check
+ * with mtp_md_status. */
+int mtp_md_run(mtp_handle* h, mtp_md* md, double* x_dev, double* v_dev, const int32_t* z_dev, const double* mass,
+               double dt, int32_t n_steps, int32_t rebuild_every, int32_t precision, double* forces_dev,
+               double* e_pot_dev, double* e_kin_dev, void* stream);
+void mtp_md_free(mtp_md* md);
 
 /* Device status word of the handle: the first device-side error recorded
  * since the last call (non-finite site energy or force, ...), then cleared.

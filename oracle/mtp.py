@@ -687,6 +687,41 @@ def maxvol(pool: np.ndarray, rows=None, delta: float = 0.01, max_iter: int = 100
 
 
 # ---------------------------------------------------------------------------
+# Molecular dynamics (the paper's throughput runs are LAMMPS MD: 100 steps of
+# 1 fs, Sec. 2.2 and Fig. 3; its examples run 1 fs MD, Sec. 3)
+# ---------------------------------------------------------------------------
+
+# LAMMPS metal units: kinetic energy of 1 amu moving at 1 A/ps, in eV.
+AMU_A2_PS2_IN_EV = 1.0364269e-4
+
+
+def velocity_verlet(model: Model, x, v, z, cell, pbc, masses, dt: float, n_steps: int, f=None):
+    """Velocity-Verlet (NVE) trajectory with the MTP forces, metal units
+    (x in A, v in A/ps, masses per species in amu, dt in ps).  Each step:
+    v += (dt/2) F/m; x += dt v; F = F(x) on a fresh neighbour list; v += (dt/2) F/m.
+    f: forces at the initial x (computed when None).  Positions are not wrapped.
+    Returns (x, v, f, e_pot [n_steps], e_kin [n_steps]) after each step."""
+    x = np.array(x, dtype=np.float64)
+    v = np.array(v, dtype=np.float64)
+    z = np.asarray(z)
+    m = np.asarray(masses, dtype=np.float64)[z][:, None] * AMU_A2_PS2_IN_EV   # eV ps^2 / A^2
+    r_cut = model.pot.r_cut
+    if f is None:
+        f = evaluate(model, x, z, cell, neighbor_list(x, cell, pbc, r_cut), want=("e", "f"))["f"]
+    f = np.array(f, dtype=np.float64)
+    e_pot, e_kin = [], []
+    for _ in range(n_steps):
+        v = v + 0.5 * dt * f / m
+        x = x + dt * v
+        out = evaluate(model, x, z, cell, neighbor_list(x, cell, pbc, r_cut), want=("e", "f"))
+        f = out["f"]
+        v = v + 0.5 * dt * f / m
+        e_pot.append(out["e"])
+        e_kin.append(float(0.5 * (m * v * v).sum()))
+    return x, v, f, np.array(e_pot), np.array(e_kin)
+
+
+# ---------------------------------------------------------------------------
 # Potential files (written by oracle/make_potentials.py)
 # ---------------------------------------------------------------------------
 

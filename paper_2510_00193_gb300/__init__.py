@@ -20,7 +20,7 @@ __all__ = [
     "MTP_FP64", "MTP_MIXED", "MTP_GRADE_TENSOR", "MTP_GRADE_FP64", "MtpError", "Potential", "NeighborList", "mtp_basis_info", "mtp_basis_table",
     "mtp_load_params", "mtp_build_neighbors", "mtp_compute_efv", "mtp_compute_efv_noalloc", "mtp_compute_grade",
     "mtp_grade_tc_selftest", "mtp_device_status", "mtp_compute_efv_tangent", "Batch", "mtp_batch_create", "mtp_compute_batch", "mtp_batch_tune",
-    "library_path",
+    "MD", "library_path",
 ]
 
 
@@ -411,3 +411,86 @@ def mtp_compute_efv_tangent(potential: Potential, nlist: NeighborList, x, z, cel
 def mtp_device_status(potential: Potential, stream=None) -> int:
     """Device-side status since the last check (0 = fine); raises on error."""
     return check(_lib.load().mtp_device_status(potential.handle, _stream_ptr(stream)))
+
+
+class MD:
+    """Owns an mtp_md: velocity-Verlet molecular dynamics with a skin
+    neighbour list filtered to the exact list every step (include/mtp.h)."""
+
+    def __init__(self, potential: Potential, x, cell, pbc=(1, 1, 1), skin=0.3, stream=None):
+        import torch
+        n = x.shape[0]
+        c = _host_d(cell, 9)
+        p = np.ascontiguousarray(np.asarray(pbc, dtype=np.int32).reshape(3))
+        self.n_atoms = n
+        self.cell = c
+        self._pot = potential
+        self._md = ctypes.c_void_p()
+        check(_lib.load().mtp_md_create(
+            potential.handle, _dptr(x, torch.float64, 3 * n, "x"), n, c.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+            p.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), float(skin), ctypes.byref(self._md), _stream_ptr(stream)))
+
+    @property
+    def handle(self):
+        return self._md
+
+    def rebuild(self, x, stream=None):
+        import torch
+        check(_lib.load().mtp_md_rebuild(self._pot.handle, self._md, _dptr(x, torch.float64, 3 * self.n_atoms, "x"),
+                                         _stream_ptr(stream)))
+
+    def nlist(self, stream=None) -> NeighborList:
+        """The exact list of the current positions (a view owned by this object)."""
+        nl = ctypes.c_void_p()
+        check(_lib.load().mtp_md_nlist(self._md, ctypes.byref(nl), _stream_ptr(stream)))
+        view = _NeighborListView()
+        view._nl = nl
+        view._owner = self
+        return view
+
+    def status(self, stream=None) -> int:
+        """Steps run on the current skin list; raises MtpError (MTP_ERR_STALE_LIST)
+        if an atom moved more than skin/2 since its build."""
+        k = ctypes.c_int64()
+        check(_lib.load().mtp_md_status(self._md, ctypes.byref(k), None, _stream_ptr(stream)))
+        return k.value
+
+    def rebuilds(self, stream=None) -> int:
+        """Skin-list builds since creation (the first included)."""
+        k = ctypes.c_int64()
+        check(_lib.load().mtp_md_status(self._md, None, ctypes.byref(k), _stream_ptr(stream)))
+        return k.value
+
+    def run(self, x, v, z, masses, dt, n_steps, forces, rebuild_every=0, precision=MTP_MIXED, e_pot=None, e_kin=None,
+            stream=None):
+        """n_steps velocity-Verlet steps in place on x, v and forces (CUDA
+        tensors [N, 3] float64; forces must hold the forces at x on entry).
+        masses: per species, amu; dt in ps.  rebuild_every: < 0 check the
+        displacements every step and rebuild when needed, > 0 rebuild every
+        that many steps, 0 never (no synchronisation).  e_pot / e_kin: optional
+        CUDA tensors [n_steps] float64 that receive the energies after each step."""
+        import torch
+        n = self.n_atoms
+        m = _host_d(masses, self._pot.n_species)
+        check(_lib.load().mtp_md_run(
+            self._pot.handle, self._md, _dptr(x, torch.float64, 3 * n, "x"), _dptr(v, torch.float64, 3 * n, "v"),
+            _dptr(z, torch.int32, n, "z"), m.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), float(dt), int(n_steps),
+            int(rebuild_every), int(precision), _dptr(forces, torch.float64, 3 * n, "forces"),
+            _dptr(e_pot, torch.float64, n_steps, "e_pot") if e_pot is not None else None,
+            _dptr(e_kin, torch.float64, n_steps, "e_kin") if e_kin is not None else None, _stream_ptr(stream)))
+
+    def __del__(self):
+        md = getattr(self, "_md", None)
+        if md is not None and md.value:
+            try:
+                _lib.load().mtp_md_free(md)
+            except Exception:
+                pass
+            self._md = None
+
+
+class _NeighborListView(NeighborList):
+    """A neighbour list owned by another object (not freed here)."""
+
+    def __del__(self):
+        self._nl = None

@@ -15,11 +15,13 @@ MTP_STATUS_BREAK = 1
 STATUS_NAMES = {
     1: "MTP_STATUS_BREAK", -1: "MTP_ERR_ARG", -2: "MTP_ERR_CUDA", -3: "MTP_ERR_OOM",
     -4: "MTP_ERR_NEIGHBOR_OVERFLOW", -5: "MTP_ERR_NONFINITE", -6: "MTP_ERR_TIMEOUT", -7: "MTP_ERR_UNSUPPORTED",
+    -8: "MTP_ERR_STALE_LIST",
 }
 MTP_FP64 = 0
 MTP_MIXED = 1
 MTP_GRADE_TENSOR = 0
 MTP_GRADE_FP64 = 1
+MTP_ERR_STALE_LIST = -8
 
 
 class MtpError(RuntimeError):
@@ -71,6 +73,13 @@ SIGNATURES = {
     "mtp_batch_tune": (ctypes.c_int, [_VP, _VP, _VP, _VP, _I32, _I32, _P_I32, _VP, _VP, _VP, _VP, _VP]),
     "mtp_batch_free": (None, [_VP]),
     "mtp_compute_efv_noalloc": (ctypes.c_int, [_VP, _VP, _VP, _VP, _I64, _P_D, _I64, _VP, _VP, _VP, _VP, _VP]),
+    "mtp_md_create": (ctypes.c_int, [_VP, _VP, _I64, _P_D, _P_I32, ctypes.c_double, ctypes.POINTER(_VP), _VP]),
+    "mtp_md_rebuild": (ctypes.c_int, [_VP, _VP, _VP, _VP]),
+    "mtp_md_nlist": (ctypes.c_int, [_VP, ctypes.POINTER(_VP), _VP]),
+    "mtp_md_status": (ctypes.c_int, [_VP, _P_I64, _P_I64, _VP]),
+    "mtp_md_run": (ctypes.c_int, [_VP, _VP, _VP, _VP, _VP, _P_D, ctypes.c_double, _I32, _I32, _I32, _VP, _VP, _VP,
+                                  _VP]),
+    "mtp_md_free": (None, [_VP]),
     "mtp_device_status": (ctypes.c_int, [_VP, _VP]),
     "mtp_last_error": (ctypes.c_char_p, []),
 }

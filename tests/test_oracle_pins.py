@@ -516,6 +516,71 @@ def test_nve_energy_error_scales_with_dt_squared():
     assert drift < 0.5 * fl2
 
 
+def test_metal_unit_constant_from_si_values():
+    """1 amu (A/ps)^2 in eV from the SI definitions (CODATA 2018 atomic mass
+    constant, exact elementary charge): the oracle's kinetic-energy constant."""
+    amu_kg = 1.66053906660e-27
+    j = amu_kg * (1e-10 / 1e-12) ** 2
+    assert O.AMU_A2_PS2_IN_EV == pytest.approx(j / 1.602176634e-19, rel=1e-7)
+
+
+def _md_start(seed, temperature=300.0, cells=(2, 2, 2)):
+    st = synth.crystal("bcc", cells, 3.16, 0.03, 1, seed)
+    mass = 183.84
+    kt = 8.617333e-5 * temperature
+    v = synth.rng(seed, 5).normal(0, math.sqrt(kt / (mass * O.AMU_A2_PS2_IN_EV)), size=(st.n, 3))
+    v -= v.mean(0)
+    return st, v, [mass]
+
+
+def test_velocity_verlet_free_flight_is_exact():
+    """With every xi = 0 the forces vanish: x_n = x_0 + n dt v_0, v and the
+    energies stay constant (the potential energy is sum_i s[z_i])."""
+    model = O.load_model(pot_file("bcc-l8-s1"))
+    model.xi = torch.zeros_like(model.xi)
+    st, v0, masses = _md_start(41)
+    dt, n = 1e-3, 4
+    x, v, f, e_pot, e_kin = O.velocity_verlet(model, st.x, v0, st.z, st.cell, st.pbc, masses, dt, n)
+    assert np.abs(f).max() == 0.0
+    assert np.allclose(x, st.x + n * dt * v0, rtol=0, atol=1e-12)
+    assert np.array_equal(v, v0)
+    s = float(model.s[0]) * st.n
+    assert np.allclose(e_pot, s, rtol=1e-14)
+    ke = 0.5 * masses[0] * O.AMU_A2_PS2_IN_EV * (v0 * v0).sum()
+    assert np.allclose(e_kin, ke, rtol=1e-14)
+
+
+def test_velocity_verlet_is_time_reversible_and_conserves_momentum():
+    """Velocity Verlet is symmetric: n steps, reversed velocities, n steps
+    return to the start; the total momentum stays constant (sum F = 0)."""
+    model = O.load_model(pot_file("bcc-l8-s1"))
+    st, v0, masses = _md_start(42)
+    dt, n = 1e-3, 6
+    x1, v1, f1, _, _ = O.velocity_verlet(model, st.x, v0, st.z, st.cell, st.pbc, masses, dt, n)
+    assert np.abs(x1 - st.x).max() > 1e-3           # it moved
+    assert np.abs(v1.sum(0) - v0.sum(0)).max() < 1e-10
+    x2, v2, _, _, _ = O.velocity_verlet(model, x1, -v1, st.z, st.cell, st.pbc, masses, dt, n, f=f1)
+    assert np.abs(x2 - st.x).max() < 1e-10
+    assert np.abs(v2 + v0).max() < 1e-8
+
+
+@pytest.mark.slow
+def test_velocity_verlet_energy_error_scales_with_dt_squared():
+    """The oracle integrator's total-energy fluctuation shrinks about 4x when
+    dt halves (second order), with no secular drift."""
+    model = O.load_model(pot_file("bcc-l8-s1"))
+    st, v0, masses = _md_start(43, temperature=50.0)
+
+    def etot(dt, n):
+        _, _, _, e_pot, e_kin = O.velocity_verlet(model, st.x, v0, st.z, st.cell, st.pbc, masses, dt, n)
+        return e_pot + e_kin
+
+    e1 = etot(2e-3, 40)
+    e2 = etot(1e-3, 80)
+    ratio = (e1.max() - e1.min()) / (e2.max() - e2.min())
+    assert 2.8 < ratio < 5.5
+
+
 # --------------------------------------------------------------------------- grade and MaxVol
 
 
