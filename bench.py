@@ -29,10 +29,10 @@ POTENTIAL = "bcc-l16-s3"
 CELLS = (80, 80, 80)
 SM_COUNT = 152
 FP32_LANES = 128
-# DRAM read + write per atom of efv_kernel<MtpLevel16, float, 0> from the ncu
-# capture in profiles/efv_kernel_bcc70_l16_mixed.md (686,000 atoms; traffic
-# scales with the atom count).  Set to None whenever that kernel changes.
-EFV_TRAFFIC_BYTES_PER_ATOM = (184.769536e6 + 142.363648e6) / 686000
+# DRAM read + write per atom of efv_kernel<MtpLevel16, float, 0> from the
+# latest ncu capture in profiles/efv_kernel_bcc70_l16_mixed.md (686,000 atoms;
+# traffic scales with the atom count).  Set to None whenever that kernel changes.
+EFV_TRAFFIC_BYTES_PER_ATOM = (185.553664e6 + 210.851072e6) / 686000
 
 
 def _peaks():
