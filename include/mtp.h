@@ -242,6 +242,32 @@ int mtp_compute_efv_noalloc(mtp_handle* h, const mtp_nlist* nl, const double* x_
                             int64_t n_atoms, const double* cell, int64_t chunk_atoms, double* e_atom_dev,
                             double* forces_dev, double* virial_dev, double* e_total_dev, void* stream);
 
+/* FP64 basis rows b_i = (B_1(i) .. B_m(i)) of every atom (the rows the
+ * extrapolation grade multiplies by A^-1; paper Sec. 2.1), e.g. to build an
+ * active-set pool for mtp_maxvol.  rows_dev: DEVICE [N][m] FP64, row-major,
+ * in the library's basis order.  Asynchronous. */
+int mtp_compute_basis_rows(mtp_handle* h, const mtp_nlist* nl, const double* x_dev, const int32_t* z_dev,
+                           int64_t n_atoms, const double* cell, double* rows_dev, void* stream);
+
+/* Active-set selection by MaxVol (Goreinov et al. 2010), the selection behind
+ * the active set A of the extrapolation grade (paper Sec. 2.1 and Sec. 2.3:
+ * configurations whose grade exceeds the selection threshold are selected for
+ * the active set).  pool_dev: DEVICE [n_pool][m] FP64 rows; rows: HOST [m]
+ * distinct pool indices, on entry the initial active rows, on return the
+ * selected ones (rows[k] is the pool row in position k of A).  Repeats
+ *   C = P A^-1, (i, k) = argmax |C_ik| (first in row-major order),
+ *   stop if |C_ik| <= 1 + delta (or after max_iter swaps), else rows[k] = i,
+ * with rank-one (Sherman-Morrison) updates of C and A^-1 and a fresh
+ * Gauss-Jordan inverse (partial pivoting) every 32 swaps and before a stop is
+ * accepted.  a_inv_dev: DEVICE [m][m] FP64, on return the inverse of the final
+ * active rows.  iterations: HOST (nullable), the number of swaps.
+ * MTP_ERR_ARG for invalid or duplicate rows or a singular active set,
+ * MTP_ERR_NONFINITE for non-finite entries.  Allocates its scratch
+ * (8 (n_pool m + 2 m^2) bytes and a little more) for the call; synchronises
+ * `stream` once per swap. */
+int mtp_maxvol(const double* pool_dev, int64_t n_pool, int32_t m, int32_t* rows, double delta, int32_t max_iter,
+               double* a_inv_dev, int32_t* iterations, void* stream);
+
 /* On-device molecular dynamics: velocity-Verlet (NVE) steps with the MTP
  * forces.  The paper measures the potential inside LAMMPS molecular dynamics
  * (100 steps of 1 fs per run, atom-timesteps per second: Sec. 2.2, Fig. 3;

@@ -20,7 +20,7 @@ __all__ = [
     "MTP_FP64", "MTP_MIXED", "MTP_GRADE_TENSOR", "MTP_GRADE_FP64", "MtpError", "Potential", "NeighborList", "mtp_basis_info", "mtp_basis_table",
     "mtp_load_params", "mtp_build_neighbors", "mtp_compute_efv", "mtp_compute_efv_noalloc", "mtp_compute_grade",
     "mtp_grade_tc_selftest", "mtp_device_status", "mtp_compute_efv_tangent", "Batch", "mtp_batch_create", "mtp_compute_batch", "mtp_batch_tune",
-    "MD", "library_path",
+    "MD", "mtp_compute_basis_rows", "mtp_maxvol", "library_path",
 ]
 
 
@@ -411,6 +411,37 @@ def mtp_compute_efv_tangent(potential: Potential, nlist: NeighborList, x, z, cel
 def mtp_device_status(potential: Potential, stream=None) -> int:
     """Device-side status since the last check (0 = fine); raises on error."""
     return check(_lib.load().mtp_device_status(potential.handle, _stream_ptr(stream)))
+
+
+def mtp_compute_basis_rows(potential: Potential, nlist: NeighborList, x, z, cell, out=None, stream=None):
+    """FP64 basis rows [N, m] (CUDA tensor) of every atom."""
+    import torch
+    n = x.shape[0]
+    if out is None:
+        out = torch.empty((n, potential.m), dtype=torch.float64, device=x.device)
+    c = _host_d(cell, 9)
+    check(_lib.load().mtp_compute_basis_rows(
+        potential.handle, nlist.handle, _dptr(x, torch.float64, 3 * n, "x"), _dptr(z, torch.int32, n, "z"), n,
+        c.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), _dptr(out, torch.float64, n * potential.m, "rows"),
+        _stream_ptr(stream)))
+    return out
+
+
+def mtp_maxvol(pool, rows, delta=0.01, max_iter=10000, stream=None):
+    """MaxVol active set of pool ([n_pool, m] float64 CUDA tensor) from the
+    initial rows; returns (rows as an int32 numpy array, A^-1 [m, m] CUDA
+    tensor, number of swaps)."""
+    import torch
+    n, m = pool.shape
+    r = np.ascontiguousarray(np.asarray(rows, dtype=np.int32).reshape(-1)).copy()
+    if r.size != m:
+        raise ValueError("rows must hold m = %d indices" % m)
+    a_inv = torch.empty((m, m), dtype=torch.float64, device=pool.device)
+    it = ctypes.c_int32()
+    check(_lib.load().mtp_maxvol(_dptr(pool, torch.float64, n * m, "pool"), n, m,
+                                 r.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), float(delta), int(max_iter),
+                                 _dptr(a_inv, torch.float64, m * m, "a_inv"), ctypes.byref(it), _stream_ptr(stream)))
+    return r, a_inv, it.value
 
 
 class MD:

@@ -73,6 +73,8 @@ SIGNATURES = {
     "mtp_batch_tune": (ctypes.c_int, [_VP, _VP, _VP, _VP, _I32, _I32, _P_I32, _VP, _VP, _VP, _VP, _VP]),
     "mtp_batch_free": (None, [_VP]),
     "mtp_compute_efv_noalloc": (ctypes.c_int, [_VP, _VP, _VP, _VP, _I64, _P_D, _I64, _VP, _VP, _VP, _VP, _VP]),
+    "mtp_compute_basis_rows": (ctypes.c_int, [_VP, _VP, _VP, _VP, _I64, _P_D, _VP, _VP]),
+    "mtp_maxvol": (ctypes.c_int, [_VP, _I64, _I32, _P_I32, ctypes.c_double, _I32, _VP, _P_I32, _VP]),
     "mtp_md_create": (ctypes.c_int, [_VP, _VP, _I64, _P_D, _P_I32, ctypes.c_double, ctypes.POINTER(_VP), _VP]),
     "mtp_md_rebuild": (ctypes.c_int, [_VP, _VP, _VP, _VP]),
     "mtp_md_nlist": (ctypes.c_int, [_VP, ctypes.POINTER(_VP), _VP]),
