@@ -184,7 +184,30 @@ def run_grade(P, torch, args):
     res["product_flops_fp64_equivalent"] = flops_fp64
     res["mma_flops_executed"] = 2.0 * 28 * 128 * 128 * 128 * ((st.n + 127) // 128)
     res["tc_kernel"] = time_tc_kernel(P, torch)
+    res["maxvol"] = time_maxvol(P, torch)
     return res
+
+
+def time_maxvol(P, torch):
+    """Active-set selection for the neighbourhood grade: MaxVol (delta 0.01)
+    over the FP64 basis rows of every atom of a 20^3-cell BCC box (16,000
+    atoms, sigma 0.05 A, level 16), from the first m rows of a seeded
+    permutation of the pool; basis rows and MaxVol both on the device."""
+    import numpy as np
+
+    import synth
+    st = synth.crystal("bcc", (20, 20, 20), 3.16, 0.05, 1, 5, sub=8)
+    pot = P.Potential.from_file(os.path.join(ROOT, "potentials", "bcc-l16-s1.json"))
+    x = torch.tensor(st.x, dtype=torch.float64, device="cuda")
+    z = torch.tensor(st.z, dtype=torch.int32, device="cuda")
+    nl = P.mtp_build_neighbors(pot, x, st.cell, st.pbc)
+    rows = P.mtp_compute_basis_rows(pot, nl, x, z, st.cell)
+    torch.cuda.synchronize()
+    init = np.random.default_rng(20251005).permutation(st.n)[:pot.m]
+    t0 = time.perf_counter()
+    sel, _, swaps = P.mtp_maxvol(rows, init, delta=0.01)
+    ms = 1e3 * (time.perf_counter() - t0)
+    return {"pool_rows": st.n, "m": pot.m, "swaps": swaps, "ms": ms, "ms_per_swap": ms / max(1, swaps)}
 
 
 def time_tc_kernel(P, torch, rows=262144, reps=5):
