@@ -9,7 +9,8 @@
 // each candidate exactly once (several images for cells thinner than R_cut).
 // The in/out decision is the exact FP64 expression of the list definition:
 // d = (x_j + s) - x_i, s = (n1 a + n2 b) + n3 c, r^2 = (dx dx + dy dy) + dz dz,
-// each operation separately rounded (explicit _rn intrinsics, no contraction).
+// each operation separately rounded (explicit _rn intrinsics, no contraction),
+// wherever an FP32 estimate with a proven error bound cannot decide it.
 #include <cub/device/device_scan.cuh>
 
 #include <algorithm>
@@ -24,6 +25,8 @@ struct NbrGeom {
   double cell[9];
   float cellf[9];
   float rc2_hi;       // prefilter bound: rc^2 plus the worst FP32 rounding of r^2
+  float rc2_lo;       // below it (and above rz2) a candidate is inside whatever the rounding
+  float rz2;          // FP32 r^2 above which the exact r^2 is certainly positive
   double hinv[9];
   double origin[3];   // fractional origin of the bin grid (0 on periodic axes)
   double width[3];    // fractional width of one bin
@@ -155,22 +158,27 @@ __global__ void pair_kernel(const double* __restrict__ x, const double* __restri
           const int j = bin_atoms[s0 + u];
           const float4 qw = xw[j];
           const float fx = qw.x + shx, fy = qw.y + shy, fz = qw.z + shz;
-          if (fx * fx + fy * fy + fz * fz >= g.rc2_hi) continue;
+          const float r2f = fx * fx + fy * fy + fz * fz;
+          if (r2f >= g.rc2_hi) continue;
           // image of j relative to the unwrapped positions
           const int n1 = q0 + wi[0] - wrapcnt[3 * j];
           const int n2 = q1 + wi[1] - wrapcnt[3 * j + 1];
           const int n3 = q2 + wi[2] - wrapcnt[3 * j + 2];
-          const double sx = __dadd_rn(__dadd_rn(__dmul_rn((double)n1, g.cell[0]), __dmul_rn((double)n2, g.cell[3])),
-                                      __dmul_rn((double)n3, g.cell[6]));
-          const double sy = __dadd_rn(__dadd_rn(__dmul_rn((double)n1, g.cell[1]), __dmul_rn((double)n2, g.cell[4])),
-                                      __dmul_rn((double)n3, g.cell[7]));
-          const double sz = __dadd_rn(__dadd_rn(__dmul_rn((double)n1, g.cell[2]), __dmul_rn((double)n2, g.cell[5])),
-                                      __dmul_rn((double)n3, g.cell[8]));
-          const double dx = __dsub_rn(__dadd_rn(x[3 * j], sx), xi);
-          const double dy = __dsub_rn(__dadd_rn(x[3 * j + 1], sy), yi);
-          const double dz = __dsub_rn(__dadd_rn(x[3 * j + 2], sz), zi);
-          const double r2 = __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
-          if (r2 < g.rc2 && r2 > 0.0) {
+          bool inside = r2f < g.rc2_lo && r2f > g.rz2;   // decided by the FP32 bound
+          if (!inside) {
+            const double sx = __dadd_rn(__dadd_rn(__dmul_rn((double)n1, g.cell[0]), __dmul_rn((double)n2, g.cell[3])),
+                                        __dmul_rn((double)n3, g.cell[6]));
+            const double sy = __dadd_rn(__dadd_rn(__dmul_rn((double)n1, g.cell[1]), __dmul_rn((double)n2, g.cell[4])),
+                                        __dmul_rn((double)n3, g.cell[7]));
+            const double sz = __dadd_rn(__dadd_rn(__dmul_rn((double)n1, g.cell[2]), __dmul_rn((double)n2, g.cell[5])),
+                                        __dmul_rn((double)n3, g.cell[8]));
+            const double dx = __dsub_rn(__dadd_rn(x[3 * j], sx), xi);
+            const double dy = __dsub_rn(__dadd_rn(x[3 * j + 1], sy), yi);
+            const double dz = __dsub_rn(__dadd_rn(x[3 * j + 2], sz), zi);
+            const double r2 = __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
+            inside = r2 < g.rc2 && r2 > 0.0;
+          }
+          if (inside) {
             if (n1 < -511 || n1 > 511 || n2 < -511 || n2 > 511 || n3 < -511 || n3 > 511) {
               atomicCAS(status, 0, MTP_ERR_NEIGHBOR_OVERFLOW);
               continue;
@@ -280,7 +288,9 @@ int build_neighbors(mtp_nlist* nl, const double* x, int64_t n, const double* cel
   int64_t nbins = 1;
   for (int k = 0; k < 3; ++k) {
     if (g.pbc[k]) {
-      g.nb[k] = std::max(1, (int)std::floor(h[k] / r_cut));
+      // bins of about half the cutoff: a reach of 2 bins searches 5^3 bins of
+      // width R_cut/2 (15.6 R_cut^3) instead of 3^3 bins of width R_cut (27 R_cut^3)
+      g.nb[k] = std::max(1, (int)std::floor(2.0 * h[k] / r_cut));
       g.nb[k] = (int)std::min<int64_t>(g.nb[k], 1024);
       g.origin[k] = 0.0;
       g.width[k] = 1.0 / g.nb[k];
@@ -320,6 +330,12 @@ int build_neighbors(mtp_nlist* nl, const double* x, int64_t n, const double* cel
     }
     const double err = 8.0 * ext * std::ldexp(1.0, -24) * std::sqrt(3.0);
     g.rc2_hi = (float)((r_cut + 2.0 * err) * (r_cut + 2.0 * err) * (1.0 + 1e-5));
+    // the same bound the other way: an FP32 distance below R_cut - 2 err (and
+    // above 4 err) puts the exact one inside (0, R_cut), so the FP64 test is
+    // needed only in the two shells of width ~4 err around 0 and R_cut
+    const double lo = r_cut - 2.0 * err;
+    g.rc2_lo = lo > 0.0 ? (float)(lo * lo * (1.0 - 1e-5)) : 0.0f;
+    g.rz2 = (float)(16.0 * err * err * (1.0 + 1e-5)) + 1e-30f;
   }
   if ((rc = nl->bins.ensure(sizeof(int) * (2 * nbins + 1))) != MTP_OK) return rc;
   int* bin_count = nl->bins.as<int>();
