@@ -511,9 +511,21 @@ def run_ours(args):
 
     # FP64 path for the mixed/FP64 ratio (a few steps)
     ms64 = None
+    mixed_err = None
     if not args.no_fp64:
-        _, per64 = timed(P.MTP_FP64, max(2, min(3, args.steps)), 1)
+        out64, per64 = timed(P.MTP_FP64, max(2, min(3, args.steps)), 1)
         ms64 = sum(per64) / len(per64)
+        # errors of the mixed path against the FP64 path (which matches the oracle to 1e-12)
+        de = (out["e_atom"] - out64["e_atom"]).abs()
+        df = out["forces"] - out64["forces"]
+        mixed_err = {"e_atom_max_abs_eV": float(de.max()),
+                     "e_total_per_atom_abs_eV": float((out["e_total"] - out64["e_total"]).abs().item() / n_atoms),
+                     "force_rms_eV_per_A": float((df * df).mean().sqrt()),
+                     "force_max_abs_eV_per_A": float(df.abs().max()),
+                     "virial_max_rel": float((out["virial"] - out64["virial"]).abs().max()
+                                             / out64["virial"].abs().max()),
+                     "targets": "1e-5 eV/atom, 1e-4 eV/A RMS"}
+        del out64
 
     # end to end through the public API: pinned host positions in, forces and energy out
     xh = torch.tensor(st.x, dtype=torch.float64).pin_memory()
@@ -580,6 +592,7 @@ def run_ours(args):
             "fp64": ({"value": world * n_atoms / (ms64 * 1e-3), "unit": UNIT, "ms_per_step": ms64}
                      if ms64 else None),
             "mixed_over_fp64": (ms64 / ms) if ms64 else None,
+            "mixed_errors_vs_fp64": mixed_err,
             "nbr_build_ms": nbr_ms,
             "roofline": {"bound": "alu", "achieved": achieved_tflops, "peak": peak_tflops, "unit": "TFLOP/s",
                          "frac": achieved_tflops / peak_tflops,

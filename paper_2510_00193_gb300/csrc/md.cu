@@ -7,7 +7,7 @@
 // Fig. 3), and its examples run 1 fs MD (Sec. 3); the pair style receives a
 // neighbour list from the MD engine (Sec. 2.3).  Here one step is
 //   v += (dt/2) F/m;  x += dt v            (md_kick_drift_kernel)
-//   exact list of x from the skin list     (md_filter_kernel count, scan, fill)
+//   exact list of x from the skin list     (md_filter_kernel, scan, md_compact_kernel)
 //   F, E_pot = MTP(x)                      (the energy/force kernels)
 //   v += (dt/2) F/m;  E_kin = sum m v^2/2  (md_kick_kernel)
 // The skin list holds every pair within R_cut + skin of the positions at its
@@ -121,23 +121,21 @@ __device__ __forceinline__ bool md_keep_pair(const double* __restrict__ x, const
 }
 
 // One warp per atom: the lanes test 32 consecutive listed pairs at a time
-// (coalesced list reads) and a ballot orders the kept ones.
-// FILL = false: counts[i] = kept pairs of atom i (the warp of i = n writes
-// counts[n] = 0 for the scan).  FILL = true: the kept pairs, in list order,
-// at out_off[i].
-template <bool FILL>
+// (coalesced list reads) and a ballot keeps the kept ones in list order,
+// packed at the start of the atom's skin-list segment of tmp_j / tmp_img;
+// counts[i] = their number (the warp of i = n writes counts[n] = 0 for the
+// scan).
 __global__ void md_filter_kernel(const double* __restrict__ x, const float4* __restrict__ xf, int64_t n, MdFilterGeom g,
                                  const int64_t* __restrict__ off, const int32_t* __restrict__ nj,
                                  const int32_t* __restrict__ nimg, int64_t* __restrict__ counts,
-                                 const int64_t* __restrict__ out_off, int32_t* __restrict__ out_j,
-                                 int32_t* __restrict__ out_img) {
+                                 int32_t* __restrict__ tmp_j, int32_t* __restrict__ tmp_img) {
   const int lane = threadIdx.x & 31;
   const int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  if (!FILL && i == n && lane == 0) counts[n] = 0;
+  if (i == n && lane == 0) counts[n] = 0;
   if (i >= n) return;   // warp-uniform
   const float4 pi = xf[i];
   const int64_t beg = off[i], end = off[i + 1];
-  int64_t w = FILL ? out_off[i] : 0;
+  int64_t w = beg;
   for (int64_t k0 = beg; k0 < end; k0 += 32) {
     const int64_t k = k0 + lane;
     bool keep = false;
@@ -148,14 +146,29 @@ __global__ void md_filter_kernel(const double* __restrict__ x, const float4* __r
       keep = md_keep_pair(x, xf, g, i, pi, j, im);
     }
     const unsigned mask = __ballot_sync(0xffffffffu, keep);
-    if (FILL && keep) {
+    if (keep) {
       const int64_t pos = w + __popc(mask & ((1u << lane) - 1u));
-      out_j[pos] = j;
-      out_img[pos] = im;
+      tmp_j[pos] = j;
+      tmp_img[pos] = im;
     }
     w += __popc(mask);
   }
-  if (!FILL && lane == 0) counts[i] = w;
+  if (lane == 0) counts[i] = w - beg;
+}
+
+// One warp per atom: moves the kept pairs of atom i from its skin-list
+// segment to out_off[i] in the exact list.
+__global__ void md_compact_kernel(int64_t n, const int64_t* __restrict__ off, const int64_t* __restrict__ out_off,
+                                  const int32_t* __restrict__ tmp_j, const int32_t* __restrict__ tmp_img,
+                                  int32_t* __restrict__ out_j, int32_t* __restrict__ out_img) {
+  const int lane = threadIdx.x & 31;
+  const int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  if (i >= n) return;
+  const int64_t src = off[i], dst = out_off[i], cnt = out_off[i + 1] - dst;
+  for (int64_t k = lane; k < cnt; k += 32) {
+    out_j[dst + k] = tmp_j[src + k];
+    out_img[dst + k] = tmp_img[src + k];
+  }
 }
 
 __global__ void md_kick_kernel(double* __restrict__ v, const double* __restrict__ f, const int32_t* __restrict__ z,
@@ -203,6 +216,7 @@ struct mtp_md {
   mtp::DevBuf xref;                 // positions at the last skin-list build [N][3]
   mtp::DevBuf xf;                   // FP32 positions and max |x| [N] float4
   mtp::DevBuf counts;               // int64 [N + 1] and the scan's temporary storage
+  mtp::DevBuf tmp;                  // kept pairs at their skin-list positions: j, then image [2][P_skin]
   size_t scan_bytes = 0;
   mtp::DevBuf e_atom, small;        // site energies [N]; virial [6], E_pot [1], flags [1]
   mtp::MdFilterGeom geom;
@@ -220,22 +234,22 @@ int md_filter(mtp_md* md, const double* x, cudaStream_t s) {
   using namespace mtp;
   const int64_t n = md->n_atoms;
   if (n == 0) return MTP_OK;
-  const int T = 256;   // 8 atoms (warps) per block; n + 1 warps for the count pass
+  const int T = 256;   // 8 atoms (warps) per block; n + 1 warps for the filter pass
   const unsigned blocks = (unsigned)((32 * (n + 1) + T - 1) / T);
   int64_t* counts = md->counts.as<int64_t>();
   void* tmp = reinterpret_cast<char*>(md->counts.ptr) + ((sizeof(int64_t) * (n + 1) + 255) & ~size_t(255));
   mtp_nlist* sl = md->skin_list;
   mtp_nlist* ex = md->exact;
-  md_filter_kernel<false><<<blocks, T, 0, s>>>(x, md->xf.as<float4>(), n, md->geom, sl->offsets.as<int64_t>(),
-                                               sl->nbr_j.as<int32_t>(), sl->nbr_img.as<int32_t>(), counts, nullptr,
-                                               nullptr, nullptr);
+  const int64_t cap = std::max<int64_t>(sl->n_pairs, 1);
+  int32_t* tmp_j = md->tmp.as<int32_t>();
+  int32_t* tmp_img = tmp_j + cap;
+  md_filter_kernel<<<blocks, T, 0, s>>>(x, md->xf.as<float4>(), n, md->geom, sl->offsets.as<int64_t>(),
+                                        sl->nbr_j.as<int32_t>(), sl->nbr_img.as<int32_t>(), counts, tmp_j, tmp_img);
   MTP_TRY_CUDA(cudaGetLastError());
   size_t tb = md->scan_bytes;
   MTP_TRY_CUDA(cub::DeviceScan::ExclusiveSum(tmp, tb, counts, ex->offsets.as<int64_t>(), (int)(n + 1), s));
-  md_filter_kernel<true><<<blocks, T, 0, s>>>(x, md->xf.as<float4>(), n, md->geom, sl->offsets.as<int64_t>(),
-                                              sl->nbr_j.as<int32_t>(), sl->nbr_img.as<int32_t>(), nullptr,
-                                              ex->offsets.as<int64_t>(), ex->nbr_j.as<int32_t>(),
-                                              ex->nbr_img.as<int32_t>());
+  md_compact_kernel<<<blocks, T, 0, s>>>(n, sl->offsets.as<int64_t>(), ex->offsets.as<int64_t>(), tmp_j, tmp_img,
+                                         ex->nbr_j.as<int32_t>(), ex->nbr_img.as<int32_t>());
   MTP_TRY_CUDA(cudaGetLastError());
   return MTP_OK;
 }
@@ -262,6 +276,7 @@ int md_rebuild(mtp_handle* h, mtp_md* md, const double* x, cudaStream_t s) {
   if ((rc = ex->offsets.ensure(sizeof(int64_t) * (n + 1))) != MTP_OK) return rc;
   if ((rc = ex->nbr_j.ensure(sizeof(int32_t) * cap)) != MTP_OK) return rc;
   if ((rc = ex->nbr_img.ensure(sizeof(int32_t) * cap)) != MTP_OK) return rc;
+  if ((rc = md->tmp.ensure(2 * sizeof(int32_t) * cap)) != MTP_OK) return rc;
   ex->n_pairs = -1;   // known after the next synchronising query
   if (n > 0) {
     MTP_TRY_CUDA(cudaMemcpyAsync(md->xref.ptr, x, sizeof(double) * 3 * n, cudaMemcpyDeviceToDevice, s));
@@ -482,6 +497,7 @@ void mtp_md_free(mtp_md* md) {
   md->xref.release();
   md->xf.release();
   md->counts.release();
+  md->tmp.release();
   md->e_atom.release();
   md->small.release();
   delete md;
