@@ -50,6 +50,24 @@ def _dist():
     return rank, world
 
 
+def max_over_ranks(ms, world, device="cuda"):
+    """The slowest rank's time per step: every rank evaluates its own replica
+    (weak scaling, no exchange on the data path), so the job's step ends when
+    the last rank's does.  One all-reduce of one number, outside the timed region."""
+    if world <= 1:
+        return ms
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(world, n_atoms_per_rank, ms):
+    """Whole-job atom-steps/s: the atoms of all replicas per slowest step."""
+    return world * n_atoms_per_rank / (ms * 1e-3)
+
+
 def _workload(cells=CELLS):
     import synth
     return synth.crystal("bcc", tuple(cells), 3.16, 0.08, 3, 2)
@@ -502,19 +520,15 @@ def run_ours(args):
     with ClockSampler(local) as clk:
         out, per = timed(P.MTP_MIXED, args.steps, args.warmup)
     clocks = clk.summary()
-    ms = sum(per) / len(per)
-    if world > 1:
-        t = torch.tensor([ms], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = t.item()
-    value = world * n_atoms / (ms * 1e-3)
+    ms = max_over_ranks(sum(per) / len(per), world)
+    value = job_rate(world, n_atoms, ms)
 
     # FP64 path for the mixed/FP64 ratio (a few steps)
     ms64 = None
     mixed_err = None
     if not args.no_fp64:
         out64, per64 = timed(P.MTP_FP64, max(2, min(3, args.steps)), 1)
-        ms64 = sum(per64) / len(per64)
+        ms64 = max_over_ranks(sum(per64) / len(per64), world)
         # errors of the mixed path against the FP64 path (which matches the oracle to 1e-12)
         de = (out["e_atom"] - out64["e_atom"]).abs()
         df = out["forces"] - out64["forces"]
@@ -550,7 +564,7 @@ def run_ours(args):
     if e2e_steps:
         e1.record(stream)
         torch.cuda.synchronize()
-        e2e_ms = e0.elapsed_time(e1) / e2e_steps
+        e2e_ms = max_over_ranks(e0.elapsed_time(e1) / e2e_steps, world)
     h2d = xh.numel() * 8 + zh.numel() * 4
     d2h = fh.numel() * 8 + 8
 
@@ -589,7 +603,7 @@ def run_ours(args):
                        "l2": "inputs larger than L2 (neighbour list %.0f MB)" % (n_pairs * 8 / 1e6),
                        "parallelism": "replicas" if world > 1 else "single GPU",
                        "mean_neighbours": round(nbar, 3)},
-            "fp64": ({"value": world * n_atoms / (ms64 * 1e-3), "unit": UNIT, "ms_per_step": ms64}
+            "fp64": ({"value": job_rate(world, n_atoms, ms64), "unit": UNIT, "ms_per_step": ms64}
                      if ms64 else None),
             "mixed_over_fp64": (ms64 / ms) if ms64 else None,
             "mixed_errors_vs_fp64": mixed_err,
@@ -607,7 +621,7 @@ def run_ours(args):
             "differentiation": diff,
             "md": md,
             "cpu_baseline": cpu,
-            "e2e": ({"value": world * n_atoms / (e2e_ms * 1e-3), "unit": UNIT, "h2d_bytes_per_step": h2d,
+            "e2e": ({"value": job_rate(world, n_atoms, e2e_ms), "unit": UNIT, "h2d_bytes_per_step": h2d,
                      "d2h_bytes_per_step": d2h} if e2e_ms else None),
             "gpu_launches": 3 * args.steps,   # fixed-point pass, energy/force kernel, FP64 force conversion
             "clocks": clocks,
