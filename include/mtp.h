@@ -261,7 +261,7 @@ int mtp_compute_basis_rows(mtp_handle* h, const mtp_nlist* nl, const double* x_d
  * Gauss-Jordan inverse (partial pivoting) every 32 swaps and before a stop is
  * accepted.  a_inv_dev: DEVICE [m][m] FP64, on return the inverse of the final
  * active rows.  iterations: HOST (nullable), the number of swaps.
- * MTP_ERR_ARG for invalid or duplicate rows or a singular active set,
+ * m <= 4096.  MTP_ERR_ARG for invalid or duplicate rows or a singular active set,
  * MTP_ERR_NONFINITE for non-finite entries.  Allocates its scratch
  * (8 (n_pool m + 2 m^2) bytes and a little more) for the call; synchronises
  * `stream` once per swap. */

@@ -290,8 +290,8 @@ int mtp_maxvol(const double* pool, int64_t n_pool, int32_t m, int32_t* rows, dou
     set_error("mtp_maxvol: invalid argument (need pool, rows, a_inv, 0 < m <= n_pool, delta >= 0, max_iter >= 0)");
     return MTP_ERR_ARG;
   }
-  if ((int64_t)n_pool * m > ((int64_t)1 << 40)) {
-    set_error("mtp_maxvol: pool too large");
+  if ((int64_t)n_pool * m > ((int64_t)1 << 40) || m > 4096) {
+    set_error("mtp_maxvol: pool too large (n_pool m <= 2^40 and m <= 4096)");
     return MTP_ERR_ARG;
   }
   std::vector<char> seen((size_t)n_pool, 0);
