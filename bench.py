@@ -586,21 +586,12 @@ def run_ours(args):
     bytes_atom = 16 + 8 * nbar + 24 + 8      # fixed-point position, (j, image) per pair, force, site energy
     hbm_achieved = bytes_atom * n_atoms / (ms * 1e-3) / 1e9
 
-    cpu = cpu1 = None
+    cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         r, dt, threads = oracle_rate(st, args.cpu_sample)
         cpu = {"value": r, "unit": UNIT, "cores": threads, "kind": "oracle",
                "sample": "%d random centre atoms of the workload (E_i with their force and virial "
                          "contributions), %.1f s" % (args.cpu_sample, dt)}
-        import torch as _t
-        n_threads = _t.get_num_threads()
-        _t.set_num_threads(1)
-        try:
-            r1, dt1, _ = oracle_rate(st, 24, seed=4)
-        finally:
-            _t.set_num_threads(n_threads)
-        cpu1 = {"value": r1, "unit": UNIT, "cores": 1, "kind": "oracle",
-                "sample": "24 random centre atoms, one thread, %.1f s" % dt1}
     if rank == 0:
         workload = WORKLOAD if args.cells == CELLS[0] else WORKLOAD.replace("80x80x80 (1,024,000", "%dx%dx%d (%d" % (
             args.cells, args.cells, args.cells, n_atoms))
@@ -630,7 +621,6 @@ def run_ours(args):
             "differentiation": diff,
             "md": md,
             "cpu_baseline": cpu,
-            "cpu_baseline_1thread": cpu1,
             "ms_per_step_median": statistics.median(per),
             "ms_per_step_min": min(per),
             "e2e": ({"value": job_rate(world, n_atoms, e2e_ms), "unit": UNIT, "h2d_bytes_per_step": h2d,
