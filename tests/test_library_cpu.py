@@ -91,3 +91,32 @@ def test_errors_are_reported_not_raised_as_crashes(lib):
     n = ctypes.c_int64()
     assert so.mtp_basis_table(16, 9, None, ctypes.byref(n)) == -1
     assert so.mtp_load_params(None, None) == -1
+
+
+def test_new_entry_points_refuse_bad_arguments_on_the_host(lib):
+    """Argument checks of the MD, MaxVol and basis-row entry points run on the
+    host before any device work (no GPU needed): each returns MTP_ERR_ARG with
+    a message."""
+    from paper_2510_00193_gb300 import _lib
+    so = _lib.load()
+    fake = ctypes.c_void_p(0x1000)   # never dereferenced: the checks fail first
+    rows = (ctypes.c_int32 * 3)(0, 1, 1)
+    it = ctypes.c_int32()
+    # duplicate initial rows
+    assert so.mtp_maxvol(fake, 10, 3, rows, 0.01, 100, fake, ctypes.byref(it), None) == -1
+    assert b"distinct" in so.mtp_last_error()
+    # row out of range, m > n_pool, negative delta, m beyond the limit
+    rows2 = (ctypes.c_int32 * 3)(0, 1, 10)
+    assert so.mtp_maxvol(fake, 10, 3, rows2, 0.01, 100, fake, None, None) == -1
+    assert so.mtp_maxvol(fake, 2, 3, rows, 0.01, 100, fake, None, None) == -1
+    assert so.mtp_maxvol(fake, 10, 3, rows, -1.0, 100, fake, None, None) == -1
+    assert so.mtp_maxvol(fake, 10 ** 6, 5000, rows, 0.01, 100, fake, None, None) == -1
+    # MD and basis rows without a handle
+    cell = (ctypes.c_double * 9)(10, 0, 0, 0, 10, 0, 0, 0, 10)
+    pbc = (ctypes.c_int32 * 3)(1, 1, 1)
+    out = ctypes.c_void_p()
+    assert so.mtp_md_create(None, fake, 4, cell, pbc, 0.3, ctypes.byref(out), None) == -1
+    assert so.mtp_md_run(None, None, fake, fake, fake, None, 1e-3, 1, 0, 1, fake, None, None, None) == -1
+    assert so.mtp_md_status(None, None, None, None) == -1
+    assert so.mtp_compute_basis_rows(None, None, fake, fake, 4, cell, fake, None) == -1
+    so.mtp_md_free(None)
