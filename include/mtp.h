@@ -193,8 +193,8 @@ int mtp_grade_tc_selftest(const uint16_t* xs_dev, const uint16_t* ys_dev, const 
                           const int32_t* erow_dev, int64_t n_rows, float* acc_dev, uint64_t* gamma_bits_dev,
                           void* stream);
 
-/* Batches of many small periodic configurations (SURVEY workload: thousands
- * of 8..256-atom cells), evaluated in one persistent launch.
+/* Batches of many small periodic configurations (for example thousands of
+ * 8..256-atom cells), evaluated in one persistent launch.
  * mtp_batch_create: atom_off (HOST, n_cfg + 1, atom_off[0] = 0) splits the
  * concatenated atoms into configurations; cells (HOST, n_cfg x 9, rows a, b,
  * c per configuration); pbc (HOST, 3, for all); x_dev the positions used to
