@@ -62,7 +62,7 @@ typedef enum { MTP_FP64 = 0, MTP_MIXED = 1 } mtp_precision;
 
 /* Potential parameters, all HOST pointers, copied by mtp_load_params. */
 typedef struct {
-  int32_t level;                 /* MTP level L (even, 2..20 in this build) */
+  int32_t level;                 /* MTP level L (even, 2..20 compiled into the library) */
   int32_t n_species;             /* S >= 1 */
   int32_t n_q;                   /* radial basis size, 1..16 */
   double r_min, r_cut;           /* radial basis interval, 0 <= r_min < r_cut */
