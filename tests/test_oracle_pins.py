@@ -614,6 +614,38 @@ def test_maxvol_reaches_a_dominant_set_found_by_brute_force():
     assert vol >= best / 3 ** 1.5 - 1e-12   # dominant submatrix bound (Goreinov et al. 2010)
 
 
+def test_invert_pivots_and_matches_closed_forms():
+    """Gauss-Jordan with partial pivoting: a permutation (zero diagonal, so
+    pivoting is required) is its own transpose inverse, exactly; a 2 x 2
+    matrix against the adjugate formula; a singular matrix is refused."""
+    perm = np.array([[0.0, 1.0, 0.0], [0.0, 0.0, 1.0], [1.0, 0.0, 0.0]])
+    assert np.array_equal(O.invert(perm), perm.T)
+    a = np.array([[3.0, -2.0], [5.0, 7.0]])
+    adj = np.array([[7.0, 2.0], [-5.0, 3.0]]) / (3.0 * 7.0 + 2.0 * 5.0)
+    assert np.allclose(O.invert(a), adj, rtol=1e-15, atol=1e-16)
+    with pytest.raises(np.linalg.LinAlgError):
+        O.invert(np.array([[1.0, 2.0], [0.0, 0.0]]))
+
+
+def test_initial_rows_greedy_order_on_orthogonal_rows():
+    """On rows that are orthogonal with distinct norms the greedy start takes
+    them by decreasing norm; rows in the span of those already taken (here a
+    scaled copy) are never taken while independent rows remain."""
+    q, _ = np.linalg.qr(synth.rng(15, 0).normal(size=(5, 5)))
+    norms = np.array([3.0, 7.0, 1.0, 5.0, 2.0])
+    pool = np.vstack([q * norms[:, None], 10.0 * q[2]])   # row 5: a longer copy of row 2's direction
+    rows = O.initial_rows(pool)
+    assert rows.tolist() == [5, 1, 3, 0, 4]
+    assert abs(np.linalg.det(pool[rows])) > 0
+
+
+def test_maxvol_ties_go_to_the_lowest_row():
+    """Two identical pool rows dominate: the swap takes the lower index."""
+    pool = np.array([[1.0, 0.0], [0.0, 1.0], [5.0, 0.5], [5.0, 0.5], [0.2, 0.1]])
+    rows, _, it = O.maxvol(pool, rows=np.array([0, 1]), delta=0.0)
+    assert it >= 1 and 2 in rows.tolist() and 3 not in rows.tolist()
+
+
 def test_grade_flags():
     gam = np.array([0.5, 2.0, 2.0000001, 9.99, 10.0, 10.5])
     assert O.grade_flags(gam, 2.0, 10.0).tolist() == [0, 0, 1, 1, 1, 3]
