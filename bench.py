@@ -142,22 +142,61 @@ class ClockSampler:
 
 
 def oracle_rate(st, n_sample, seed=3):
-    """Oracle E+F throughput on a bounded sample of centre atoms."""
+    """Oracle E+F throughput on a bounded sample of centre atoms: the sampled
+    centres' neighbour rows are built first (outside the timer), then the
+    oracle's evaluation of their site energies with force and virial
+    contributions is timed, so the cost per atom does not depend on the
+    sample size.  Returns (atom-steps/s, seconds, threads used, host cores)."""
     import numpy as np
     import torch
 
     from oracle import mtp as O
-    from tests.helpers import min_image_candidates, pot_dict
+    from tests.helpers import BinnedCandidates, oracle_rows, pot_dict
 
     model = O.load_model(pot_dict(POTENTIAL))
     g = np.random.default_rng(seed)
     centres = np.sort(g.choice(st.n, n_sample, replace=False))
-    cand = min_image_candidates(st, centres, 5.5)
+    cands = BinnedCandidates(st, 5.5)
+    rows = [oracle_rows(st, 5.0, c, cands(c)) for c in centres]
+    nl = (np.concatenate([np.full(len(r[0]), c) for c, r in zip(centres, rows)]),
+          np.concatenate([r[0] for r in rows]), np.concatenate([r[1] for r in rows]))
     t0 = time.perf_counter()
-    nl = O.neighbor_list(st.x, st.cell, st.pbc, 5.0, query=centres, candidates=cand)
     O.evaluate(model, st.x, st.z, st.cell, nl, want=("e", "f", "w"), atoms=centres)
     dt = time.perf_counter() - t0
-    return n_sample / dt, dt, torch.get_num_threads()
+    return n_sample / dt, dt, torch.get_num_threads(), os.cpu_count()
+
+
+MIXED_KAPPA = 64.0
+MIXED_BOUND = ("|dE_i| <= 1e-5 eV + 64 u a_i and |dF_k| <= 1e-4 eV/A + 64 u A_k / A, u = 2^-24, "
+               "a_i = sum_alpha |xi_alpha B_alpha(i)|, A_k = a_k + sum over neighbours j of k of a_j; "
+               "*_bound_use = max over atoms of error / bound")
+
+
+def mixed_conditioning(P, torch, pot, nl, x, z, cell, pot_name):
+    """a_i = sum_alpha |xi_alpha B_alpha(i)| (from the FP64 basis rows) and
+    A_k = a_k + sum over the neighbours j of k of a_j, the conditioning of the
+    site energies and forces that scales the mixed-precision error bound."""
+    with open(os.path.join(ROOT, "potentials", pot_name + ".json")) as fh:
+        xi = torch.tensor(json.load(fh)["xi"], dtype=torch.float64, device="cuda").abs()
+    n = x.shape[0]
+    rows = P.mtp_compute_basis_rows(pot, nl, x, z, cell)
+    a = (rows.abs() * xi).sum(1)
+    del rows
+    off, j, _ = nl.to_tensors()
+    ii = torch.repeat_interleave(torch.arange(n, device="cuda"), off[1:] - off[:-1])
+    A = a.clone().index_add_(0, ii, a[j.long()])
+    return {"a": a, "A": A}
+
+
+def fma_peaks(P, local):
+    """Measured FMA throughput of this GPU (FP32 and FP64), with the SM clock
+    sampled while the probe kernels ran."""
+    with ClockSampler(local) as clk:
+        fp32 = max(P.mtp_probe_fma(P.PROBE_FP32, 4096, 4)["flops_per_s"] for _ in range(3))
+        fp64 = max(P.mtp_probe_fma(P.PROBE_FP64, 256, 4)["flops_per_s"] for _ in range(3))
+    return {"fp32_tflops": fp32 / 1e12, "fp64_tflops": fp64 / 1e12, "clocks": clk.summary(),
+            "how": "mtp_probe_fma: 152 x 4 blocks of 256 threads, 8 independent fma chains per thread, "
+                   "CUDA events, best of 3"}
 
 
 def run_grade(P, torch, args):
@@ -364,9 +403,17 @@ def run_diff(P, torch, args):
                      "atom_steps_per_s": st.n / (ms_e * 1e-3)}
     (om, tm), (od, td) = outs["mixed"], outs["fp64"]
     import numpy as np
+    cond = mixed_conditioning(P, torch, pot, nl, x, z, st.cell, "fcc-l20-s4")
+    de = (om["e_atom"] - od["e_atom"]).abs()
+    dfa = (om["forces"] - od["forces"]).abs().max(1).values
     res["mixed_errors_vs_fp64"] = {
-        "e_atom_max_abs": float((om["e_atom"] - od["e_atom"]).abs().max()),
+        "e_atom_max_abs": float(de.max()),
         "force_rms": float(((om["forces"] - od["forces"]) ** 2).mean().sqrt()),
+        "force_max_abs": float(dfa.max()),
+        "e_total_per_atom_abs": float((om["e_total"] - od["e_total"]).abs().item() / st.n),
+        "bound": MIXED_BOUND,
+        "e_atom_bound_use": float((de / (1e-5 + MIXED_KAPPA * 2.0 ** -24 * cond["a"])).max()),
+        "force_bound_use": float((dfa / (1e-4 + MIXED_KAPPA * 2.0 ** -24 * cond["A"])).max()),
         "dtheta_max_rel": float((om["dtheta"] - od["dtheta"]).abs().max() / od["dtheta"].abs().max()),
         "dtheta_tan_max_rel": float((tm["dtheta_tan"] - td["dtheta_tan"]).abs().max()
                                     / td["dtheta_tan"].abs().max())}
@@ -432,6 +479,39 @@ def run_md(P, torch, st, pot, z, args):
     t0 = time.perf_counter()
     md.rebuild(x)
     rebuild_ms = 1e3 * (time.perf_counter() - t0)
+    # the same steps replayed from a CUDA graph of 10 steps (no synchronisation
+    # inside; the displacement check runs between replays every 20 steps,
+    # outside the graph).  A rebuild may move the list buffers, which a
+    # captured graph holds by address, so a caller that rebuilds captures
+    # again; these 0.01 fs steps need no rebuild (checked).
+    x.copy_(x0)
+    v.copy_(v0)
+    f.copy_(f0)
+    md.rebuild(x)
+    gs = torch.cuda.Stream()
+    with torch.cuda.stream(gs):
+        md.run(x, v, z, MD_MASSES, dt, 10, f, rebuild_every=0, precision=P.MTP_MIXED, stream=gs)
+    torch.cuda.synchronize()
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph, stream=gs):
+        md.run(x, v, z, MD_MASSES, dt, 10, f, rebuild_every=0, precision=P.MTP_MIXED, stream=gs)
+    x.copy_(x0)
+    v.copy_(v0)
+    f.copy_(f0)
+    md.rebuild(x)
+    torch.cuda.synchronize()
+    g_times = []
+    with torch.cuda.stream(gs):
+        for rep in range(3):
+            t0 = time.perf_counter()
+            for k in range(steps // 10):
+                graph.replay()
+                if k % 2 == 1:
+                    md.status(stream=gs)     # displacement check (synchronises; raises if stale)
+            gs.synchronize()
+            g_times.append(1e3 * (time.perf_counter() - t0))
+    graph_ms = min(g_times) / steps
+    del graph
     return {"workload": "bcc-80x80x80 (1,024,000 atoms), level 16, 3 species (%.2f, %.2f, %.2f amu), 300 K"
                         % MD_MASSES,
             "integrator": "velocity Verlet (NVE), dt 0.01 fs, mixed-precision forces",
@@ -442,7 +522,62 @@ def run_md(P, torch, st, pot, z, args):
             "atom_steps_per_s": st.n / (ms * 1e-3), "ns_per_day_at_1fs": 86400 / (ms * 1e-3) * 1e-6,
             "skin_list_rebuild_ms": rebuild_ms,
             "ms_per_step_with_a_rebuild_every_20_steps": ms + rebuild_ms / 20,
+            "graph_replay_ms_per_step": graph_ms,
+            "graph_replay_ms_per_step_with_a_rebuild_every_20_steps": graph_ms + rebuild_ms / 20,
+            "graph_note": "10-step CUDA graphs (rebuild_every = 0); the displacement check between replays every "
+                          "20 steps; host wall clock per step, best of 3 runs of %d steps; the rebuild figure adds "
+                          "the measured skin-list rebuild / 20" % steps,
             "total_energy_change_per_atom_eV": drift}
+
+
+def run_md_graded(P, torch, args):
+    """MD with the extrapolation grade every 10 steps (paper Sec. 2.3): the
+    500,000-atom grade workload (BCC 50 x 50 x 100, sigma 0.15 A, level 16,
+    one species, its MaxVol active set), 100 velocity-Verlet steps of 0.01 fs
+    at 300 K with mixed-precision forces and the tensor-core grade."""
+    import numpy as np
+
+    import synth
+    with open(os.path.join(ROOT, "potentials", "bcc-l16-s1-active.json")) as fh:
+        act = json.load(fh)
+    m = act["m"]
+    st = synth.crystal("bcc", (50, 50, args.grade_cells), 3.16, 0.15, 1, 5)
+    pot = P.Potential.from_file(os.path.join(ROOT, "potentials", "bcc-l16-s1.json"))
+    masses = (183.84,)
+    kb, mvv2e = 8.617333e-5, 1.0364269e-4
+    g = np.random.default_rng(20251003)
+    v0 = g.normal(size=(st.n, 3)) * np.sqrt(kb * 300.0 / (masses[0] * mvv2e))
+    v0 -= v0.mean(0)
+    x = torch.tensor(st.x, device="cuda")
+    v = torch.tensor(v0, device="cuda")
+    z = torch.tensor(st.z, dtype=torch.int32, device="cuda")
+    a_inv = torch.tensor(act["a_inv"], dtype=torch.float64, device="cuda").reshape(m, m)
+    md = P.MD(pot, x, st.cell, st.pbc, skin=0.3)
+    f = P.mtp_compute_efv(pot, md.nlist(), x, z, st.cell, precision=P.MTP_MIXED)["forces"]
+    sel = torch.zeros(st.n, dtype=torch.uint8, device="cuda")
+    md.set_grade(a_inv, 10, 2.0, 1e30, P.MTP_GRADE_TENSOR, sel)
+    md.run(x, v, z, masses, 1e-5, 10, f, rebuild_every=-1, precision=P.MTP_MIXED)   # warm-up (sizes scratch)
+    torch.cuda.synchronize()
+    steps = 100
+    t0 = time.perf_counter()
+    status = md.run(x, v, z, masses, 1e-5, steps, f, rebuild_every=-1, precision=P.MTP_MIXED)
+    torch.cuda.synchronize()
+    ms = 1e3 * (time.perf_counter() - t0) / steps
+    info = md.info()
+    md.set_grade(None, 0)
+    t0 = time.perf_counter()
+    md.run(x, v, z, masses, 1e-5, steps, f, rebuild_every=-1, precision=P.MTP_MIXED)
+    torch.cuda.synchronize()
+    ms_plain = 1e3 * (time.perf_counter() - t0) / steps
+    return {"workload": "bcc-50x50x%d (%d atoms), level 16, 1 species, sigma 0.15 A, 300 K, dt 0.01 fs"
+                        % (args.grade_cells, st.n),
+            "grade_every": 10, "tau_sel": 2.0, "steps": steps, "status": int(status),
+            "ms_per_step": ms, "ms_per_step_without_grade": ms_plain,
+            "atom_steps_per_s": st.n / (ms * 1e-3), "grade_evals": info["grade_evals"],
+            "gamma_max_last": info["gamma_max_last"], "n_selected_last": info["n_selected_last"],
+            "atoms_selected_during_run": int((sel & 1).sum().item()),
+            "timing": "host wall clock around the run (the grade synchronises every 10 steps, the "
+                      "displacement check every step)"}
 
 
 def run_reference(args):
@@ -456,7 +591,7 @@ def run_reference(args):
         oracle_rate(st, 8)
     t_total = 0.0
     for k in range(args.steps):
-        r, dt, threads = oracle_rate(st, n_sample, seed=100 + k)
+        r, dt, threads, cores = oracle_rate(st, n_sample, seed=100 + k)
         rates.append(r)
         t_total += dt
     value = n_sample * args.steps / t_total
@@ -465,9 +600,9 @@ def run_reference(args):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t_total / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": WORKLOAD, "precision": "fp64 (oracle)"},
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "host_cores": cores, "kind": "oracle",
                          "sample": "%d random centre atoms of the workload per step (E_i and their force and "
-                                   "virial contributions)" % n_sample},
+                                   "virial contributions; neighbour rows built outside the timer)" % n_sample},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line))
@@ -490,6 +625,7 @@ def run_ours(args):
     x = torch.tensor(st.x, dtype=torch.float64, device="cuda")
     z = torch.tensor(st.z, dtype=torch.int32, device="cuda")
     stream = torch.cuda.current_stream()
+    peaks = fma_peaks(P, local)
 
     # neighbour list (timed separately)
     nl = P.mtp_build_neighbors(pot, x, st.cell, st.pbc)
@@ -532,7 +668,12 @@ def run_ours(args):
         # errors of the mixed path against the FP64 path (which matches the oracle to 1e-12)
         de = (out["e_atom"] - out64["e_atom"]).abs()
         df = out["forces"] - out64["forces"]
+        cond = mixed_conditioning(P, torch, pot, nl, x, z, st.cell, POTENTIAL)
         mixed_err = {"e_atom_max_abs_eV": float(de.max()),
+                     "bound": MIXED_BOUND,
+                     "e_atom_bound_use": float((de / (1e-5 + MIXED_KAPPA * 2.0 ** -24 * cond["a"])).max()),
+                     "force_bound_use": float((df.abs().max(1).values
+                                               / (1e-4 + MIXED_KAPPA * 2.0 ** -24 * cond["A"])).max()),
                      "e_total_per_atom_abs_eV": float((out["e_total"] - out64["e_total"]).abs().item() / n_atoms),
                      "force_rms_eV_per_A": float((df * df).mean().sqrt()),
                      "force_max_abs_eV_per_A": float(df.abs().max()),
@@ -565,6 +706,26 @@ def run_ours(args):
         e1.record(stream)
         torch.cuda.synchronize()
         e2e_ms = max_over_ranks(e0.elapsed_time(e1) / e2e_steps, world)
+    # the same with the neighbour list rebuilt from each step's positions (a
+    # caller whose positions change between calls; the build synchronises)
+    e2e_nb_ms = None
+    if e2e_steps:
+        nl2 = P.mtp_build_neighbors(pot, x, st.cell, st.pbc)
+        nb_steps = max(3, e2e_steps // 4)
+        for k in range(args.warmup + nb_steps):
+            if k == args.warmup:
+                torch.cuda.synchronize()
+                e0.record(stream)
+            xd.copy_(xh, non_blocking=True)
+            zd.copy_(zh, non_blocking=True)
+            nl2 = P.mtp_build_neighbors(pot, xd, st.cell, st.pbc, nlist=nl2)
+            o = P.mtp_compute_efv(pot, nl2, xd, zd, st.cell, precision=P.MTP_MIXED, out=out)
+            fh.copy_(o["forces"], non_blocking=True)
+            eh.copy_(o["e_total"], non_blocking=True)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        e2e_nb_ms = max_over_ranks(e0.elapsed_time(e1) / nb_steps, world)
+        del nl2
     h2d = xh.numel() * 8 + zh.numel() * 4
     d2h = fh.numel() * 8 + 8
 
@@ -572,26 +733,30 @@ def run_ours(args):
     batch = None if args.no_batch else run_batch(P, torch, args)
     diff = None if args.no_diff else run_diff(P, torch, args)
     md = None
+    md_graded = None
     if not args.no_md:
         try:
             md = run_md(P, torch, st, pot, z, args)
         except P.MtpError as err:   # e.g. MTP_ERR_STALE_LIST: reported, the headline stands
             md = {"error": str(err)}
+        try:
+            md_graded = run_md_graded(P, torch, args)
+        except P.MtpError as err:
+            md_graded = {"error": str(err)}
 
     hbm_gbs, max_mhz, peak_src = _peaks()
     flops_atom, fc = _flops_per_atom(pot.level, pot.n_q, pot.n_mu, nbar)
-    mhz = max_mhz
-    peak_tflops = SM_COUNT * FP32_LANES * 2 * mhz * 1e6 / 1e12
+    peak_tflops = peaks["fp32_tflops"]
     achieved_tflops = flops_atom * n_atoms / (ms * 1e-3) / 1e12
     bytes_atom = 16 + 8 * nbar + 24 + 8      # fixed-point position, (j, image) per pair, force, site energy
     hbm_achieved = bytes_atom * n_atoms / (ms * 1e-3) / 1e9
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
-        r, dt, threads = oracle_rate(st, args.cpu_sample)
-        cpu = {"value": r, "unit": UNIT, "cores": threads, "kind": "oracle",
+        r, dt, threads, cores = oracle_rate(st, args.cpu_sample)
+        cpu = {"value": r, "unit": UNIT, "cores": threads, "host_cores": cores, "kind": "oracle",
                "sample": "%d random centre atoms of the workload (E_i with their force and virial "
-                         "contributions), %.1f s" % (args.cpu_sample, dt)}
+                         "contributions; neighbour rows built outside the timer), %.1f s" % (args.cpu_sample, dt)}
     if rank == 0:
         workload = WORKLOAD if args.cells == CELLS[0] else WORKLOAD.replace("80x80x80 (1,024,000", "%dx%dx%d (%d" % (
             args.cells, args.cells, args.cells, n_atoms))
@@ -612,19 +777,27 @@ def run_ours(args):
                          "frac": achieved_tflops / peak_tflops,
                          "traffic": (EFV_TRAFFIC_BYTES_PER_ATOM * n_atoms
                                      if EFV_TRAFFIC_BYTES_PER_ATOM and args.cells == CELLS[0] else None),
-                         "peak_source": "152 SMs x 128 FP32 lanes x 2 flop x %.0f MHz (max SM clock)" % mhz,
+                         "peak_source": "measured (FP32 fma probe on this GPU, %s; SM clock %s MHz during the "
+                                        "probe; nominal %.1f TFLOP/s = 152 SMs x 128 lanes x 2 x %.0f MHz)"
+                                        % (peaks["how"], peaks["clocks"].get("sm_mhz"),
+                                           SM_COUNT * FP32_LANES * 2 * max_mhz * 1e-6, max_mhz),
                          "flops_per_atom": flops_atom},
+            "fma_peaks_measured": peaks,
             "hbm": {"achieved": hbm_achieved, "peak": hbm_gbs, "unit": "GB/s", "frac": hbm_achieved / hbm_gbs,
                     "bytes_per_atom": bytes_atom, "peak_source": peak_src},
             "grade": grade,
             "batch": batch,
             "differentiation": diff,
             "md": md,
+            "md_with_grade": md_graded,
             "cpu_baseline": cpu,
             "ms_per_step_median": statistics.median(per),
             "ms_per_step_min": min(per),
             "e2e": ({"value": job_rate(world, n_atoms, e2e_ms), "unit": UNIT, "h2d_bytes_per_step": h2d,
                      "d2h_bytes_per_step": d2h} if e2e_ms else None),
+            "e2e_with_neighbor_build": ({"value": job_rate(world, n_atoms, e2e_nb_ms), "unit": UNIT,
+                                         "ms_per_step": e2e_nb_ms, "h2d_bytes_per_step": h2d,
+                                         "d2h_bytes_per_step": d2h} if e2e_nb_ms else None),
             "gpu_launches": 3 * args.steps,   # fixed-point pass, energy/force kernel, FP64 force conversion
             "clocks": clocks,
         }

@@ -98,6 +98,13 @@ int mtp_load_params(const mtp_params_desc* desc, mtp_handle** out);
 void mtp_free(mtp_handle* h);
 /* Number of entries of theta (see the header comment). */
 int mtp_param_count(const mtp_handle* h, int64_t* n_params);
+/* Replaces the handle's parameters by theta_dev (DEVICE [n_params] FP64, the
+ * theta layout of the header comment), queued on `stream`: later work on the
+ * handle evaluates the new potential (the training loop of the paper's
+ * MLIP-3 workflow changes theta between evaluations; Sec. 2.1).  A non-finite
+ * entry is recorded in the device status word (mtp_device_status).
+ * Asynchronous; theta_dev must stay valid until the copy has run. */
+int mtp_set_theta(mtp_handle* h, const double* theta_dev, void* stream);
 
 /* Full neighbour list (paper Sec. 2.3 needs a neighbour list; this one is
  * full, not half): every (j, n) with r_ij = x_j + n.H - x_i and
@@ -123,7 +130,12 @@ void mtp_free_nlist(mtp_nlist* nl);
  * cell (image shifts are n.H with this H).
  * precision: MTP_FP64, or MTP_MIXED (radial basis, moments, contractions and
  * the adjoint in FP32; pair vectors from 32.32 fixed-point fractional
- * coordinates; energies, forces, virial and gradients accumulated in FP64).
+ * coordinates; forces accumulated by FP32 atomics in a library-owned [N][3]
+ * buffer and converted to FP64 once; site energies, the total energy, the
+ * virial and dE/dtheta reduced in FP64 (per-thread and per-block partial sums
+ * of the virial and dE/dtheta are FP32)).  Mixed-precision error: a site's
+ * energy error grows with sum_alpha |xi_alpha B_alpha(i)|, the conditioning
+ * of its basis sum (FP32 rounding times that sum).
  * chunk_atoms: centre atoms per launch (the chunk size of paper Sec. 2.3); 0 = all.
  * Outputs (DEVICE, overwritten): e_atom [N], forces [N][3], virial [6],
  * e_total [1]; dEdtheta [n_params] or NULL to skip the parameter gradient. */
@@ -188,10 +200,22 @@ int mtp_compute_grade(mtp_handle* h, const mtp_nlist* nl, const double* x_dev, c
  * Outputs (DEVICE): acc_dev (nullable) [n_rows][2][7][64] FP32 slice-group
  * sums G_d = sum_{s+t=d} X_s Y_t for d = 2..8 per column half;
  * gamma_bits_dev [n_rows] the FP64 bit patterns of the grades.
- * Synchronises `stream`. */
+ * Synchronises `stream`; MTP_ERR_TIMEOUT if a device-side wait gave up
+ * (mtp_set_wait_limit). */
 int mtp_grade_tc_selftest(const uint16_t* xs_dev, const uint16_t* ys_dev, const int32_t* fexp_dev,
                           const int32_t* erow_dev, int64_t n_rows, float* acc_dev, uint64_t* gamma_bits_dev,
                           void* stream);
+
+/* Limit, in nanoseconds, of each pipeline wait of the tensor-core grade
+ * kernel (mbarrier waits between its copy, MMA and epilogue roles) for the
+ * launches that follow; ns < 0 restores the default of 1 s.  A wait that runs
+ * out sets MTP_ERR_TIMEOUT: the kernel then stops issuing work, waits (up to
+ * 1 s, whatever this limit) for the copies and MMAs it has already issued,
+ * frees its Tensor Memory and returns, so the context stays usable.  The
+ * paper has no counterpart; the setting exists so that the timeout path can be
+ * exercised by a test.  Process-wide, not thread-safe against concurrent
+ * launches. */
+int mtp_set_wait_limit(int64_t ns);
 
 /* Batches of many small periodic configurations (for example thousands of
  * 8..256-atom cells), evaluated in one persistent launch.
@@ -237,7 +261,10 @@ void mtp_batch_free(mtp_batch* b);
  * array's device address (cudaGetSymbolAddress, with that device current);
  * make that first call before any stream capture starts.  All calls on a
  * device share the scratch array, so calls that overlap on the GPU race:
- * issue them one after another.  Arguments and outputs as mtp_compute_efv. */
+ * issue them one after another.  Levels 18 and 20 run here as one fused
+ * kernel (mtp_compute_efv splits them into three kernels through a scratch
+ * buffer it allocates): same results, about 3.4x slower at level 20.
+ * Arguments and outputs as mtp_compute_efv. */
 int mtp_compute_efv_noalloc(mtp_handle* h, const mtp_nlist* nl, const double* x_dev, const int32_t* z_dev,
                             int64_t n_atoms, const double* cell, int64_t chunk_atoms, double* e_atom_dev,
                             double* forces_dev, double* virial_dev, double* e_total_dev, void* stream);
@@ -284,8 +311,9 @@ int mtp_maxvol(const double* pool_dev, int64_t n_pool, int32_t m, int32_t* rows,
  * the image vectors of the skin list stay valid between builds.
  *
  * mtp_md_create: builds the skin list of x_dev [N][3] (DEVICE) in the cell
- * (host [9]) with pbc (host [3]) and the exact list; the cell is fixed for
- * the life of the object.  Synchronises `stream`.  Free with mtp_md_free. */
+ * (host [9]) with pbc (host [3]) and the exact list; the cell changes only
+ * under the barostat (mtp_md_set_barostat; mtp_md_info returns it).
+ * Synchronises `stream`.  Free with mtp_md_free. */
 typedef struct mtp_md mtp_md;
 int mtp_md_create(mtp_handle* h, const double* x_dev, int64_t n_atoms, const double* cell, const int32_t* pbc,
                   double skin, mtp_md** out, void* stream);
@@ -322,6 +350,38 @@ int mtp_md_status(mtp_md* md, int64_t* steps_since_build, int64_t* rebuilds, voi
 int mtp_md_run(mtp_handle* h, mtp_md* md, double* x_dev, double* v_dev, const int32_t* z_dev, const double* mass,
                double dt, int32_t n_steps, int32_t rebuild_every, int32_t precision, double* forces_dev,
                double* e_pot_dev, double* e_kin_dev, void* stream);
+/* Extrapolation control inside mtp_md_run (paper Sec. 2.3: the grade is
+ * evaluated every X steps of the MD run; configurations above the selection
+ * threshold are kept for the active set and a grade above the break threshold
+ * halts the run).  After every `every`-th step (counted since creation) the
+ * neighbourhood grade of the current configuration is computed as
+ * mtp_compute_grade does (a_inv_dev: DEVICE m x m FP64 inverse of the active
+ * set, kept by reference; method MTP_GRADE_TENSOR or MTP_GRADE_FP64);
+ * selected_dev (DEVICE [N] uint8, nullable) accumulates each atom's flags by
+ * bitwise or (bit 0: grade above tau_sel, bit 1: above tau_brk at some
+ * evaluation).  When the largest grade exceeds tau_brk, mtp_md_run returns
+ * MTP_STATUS_BREAK right after that step (positions, velocities and forces
+ * are those of the completed step).  Each evaluation synchronises the stream.
+ * a_inv_dev = NULL or every <= 0 switches the grade off.  Allocates the
+ * grade outputs (12 bytes per atom) once. */
+int mtp_md_set_grade(mtp_handle* h, mtp_md* md, const double* a_inv_dev, int32_t every, double tau_sel,
+                     double tau_brk, int32_t method, uint8_t* selected_dev);
+/* Berendsen barostat for NPT runs (the paper's examples run NPT MD, Sec. 3),
+ * isotropic: after each step the pressure P = (2 E_kin + W_xx + W_yy + W_zz) /
+ * (3 V) (bar, from the FP64 virial of the step's forces) sets
+ * mu = (1 - (dt / tau_p) (p_target - P) / bulk_modulus)^(1/3), and the
+ * positions, the cell and the skin list's reference positions are scaled by
+ * mu (the LAMMPS fix press/berendsen form, "iso" coupling; bulk modulus in
+ * bar, LAMMPS default 10).  The skin criterion accounts for the compression
+ * since the last build.  Each step then reads the pressure on the host (one
+ * synchronisation per step).  tau_p_ps <= 0 switches it off (NVE). */
+int mtp_md_set_barostat(mtp_md* md, double p_target_bar, double tau_p_ps, double bulk_modulus_bar);
+/* Host-side record of the run (all nullable): steps run since creation,
+ * grade evaluations, the largest grade and the number of atoms above tau_sel
+ * at the last evaluation, the last barostat pressure (bar) and the current
+ * cell (HOST [9]). */
+int mtp_md_info(const mtp_md* md, int64_t* steps_total, int64_t* grade_evals, double* gamma_max_last,
+                int64_t* n_selected_last, double* pressure_last_bar, double* cell);
 void mtp_md_free(mtp_md* md);
 
 /* Device status word of the handle: the first device-side error recorded
@@ -331,6 +391,17 @@ int mtp_device_status(mtp_handle* h, void* stream);
 
 /* Human-readable message for the last failure on this thread. */
 const char* mtp_last_error(void);
+
+/* Measurement aid (no counterpart in the paper): the FMA throughput of the
+ * current device, the denominator of the arithmetic roofline of the
+ * energy/force kernels.  kind 0: FP32 fma; 1: FP64 fma; 2: packed FP32 pairs
+ * (fma.rn.f32x2).  A kernel of blocks_per_sm (1..32) blocks of 256 threads
+ * per SM runs iters x 16 x 8 dependent-in-8-chains multiply-adds per thread
+ * once to warm up and once under CUDA events on the legacy default stream.
+ * flops_per_s (HOST): 2 x multiply-adds / elapsed time; ms (HOST): elapsed
+ * time.  Allocates and frees a small output buffer; synchronises the
+ * device's default stream; changes no device setting. */
+int mtp_probe_fma(int32_t kind, int64_t iters, int32_t blocks_per_sm, double* flops_per_s, double* ms);
 
 #ifdef __cplusplus
 }

@@ -332,22 +332,6 @@ def prune_dependent(rows: np.ndarray, rel_tol: float = 1e-9) -> list:
     return kept
 
 
-def residual_norms(rows: np.ndarray) -> np.ndarray:
-    """Residual norms of the greedy pass above (diagnostic for the gap)."""
-    a = rows / np.linalg.norm(rows, axis=0, keepdims=True)
-    basis, res = [], []
-    for k in range(a.shape[1]):
-        v = a[:, k].copy()
-        for _ in range(2):
-            for q in basis:
-                v -= (q @ v) * q
-        nrm = np.linalg.norm(v)
-        res.append(nrm)
-        if nrm > 1e-9:
-            basis.append(v / nrm)
-    return np.array(res)
-
-
 @dataclasses.dataclass
 class Basis:
     level: int
@@ -719,6 +703,50 @@ def velocity_verlet(model: Model, x, v, z, cell, pbc, masses, dt: float, n_steps
         e_pot.append(out["e"])
         e_kin.append(float(0.5 * (m * v * v).sum()))
     return x, v, f, np.array(e_pot), np.array(e_kin)
+
+
+EV_PER_A3_IN_BAR = 1.602176634e-19 / 1e-30 / 1e5   # 1 eV/A^3 in bar (SI definitions)
+
+
+def pressure_bar(e_kin: float, virial, cell) -> float:
+    """Instantaneous pressure of a periodic system in bar:
+    P = (2 E_kin + W_xx + W_yy + W_zz) / (3 V), with W = -dE/d(strain) the
+    pressure virial and V = |det H|."""
+    vol = abs(float(np.linalg.det(np.asarray(cell, dtype=np.float64))))
+    return (2.0 * e_kin + float(virial[0] + virial[1] + virial[2])) / (3.0 * vol) * EV_PER_A3_IN_BAR
+
+
+def berendsen_npt(model: Model, x, v, z, cell, pbc, masses, dt: float, n_steps: int, p_target: float,
+                  tau_p: float, bulk_modulus: float = 10.0, f=None, w=None):
+    """Velocity Verlet with the Berendsen barostat (isotropic coupling; Berendsen
+    et al. 1984): each step is the velocity-Verlet step of velocity_verlet, then
+    the pressure P of the new velocities and of the virial of the new forces,
+    and the positions and the cell rows are multiplied by
+    mu = (1 - (dt / tau_p) (p_target - P) / bulk_modulus)^(1/3).
+    Pressures and the modulus in bar, tau_p in ps.  f, w: forces and virial at
+    the initial x (computed when None).  Returns (x, v, f, cell, pressures [n_steps])."""
+    x = np.array(x, dtype=np.float64)
+    v = np.array(v, dtype=np.float64)
+    cell = np.array(cell, dtype=np.float64)
+    z = np.asarray(z)
+    m = np.asarray(masses, dtype=np.float64)[z][:, None] * AMU_A2_PS2_IN_EV
+    r_cut = model.pot.r_cut
+    if f is None:
+        f = evaluate(model, x, z, cell, neighbor_list(x, cell, pbc, r_cut), want=("e", "f"))["f"]
+    f = np.array(f, dtype=np.float64)
+    pressures = []
+    for _ in range(n_steps):
+        v = v + 0.5 * dt * f / m
+        x = x + dt * v
+        out = evaluate(model, x, z, cell, neighbor_list(x, cell, pbc, r_cut), want=("e", "f", "w"))
+        f = out["f"]
+        v = v + 0.5 * dt * f / m
+        p = pressure_bar(float(0.5 * (m * v * v).sum()), out["w"], cell)
+        pressures.append(p)
+        mu = (1.0 - dt / tau_p * (p_target - p) / bulk_modulus) ** (1.0 / 3.0)
+        x = x * mu
+        cell = cell * mu
+    return x, v, f, cell, np.array(pressures)
 
 
 # ---------------------------------------------------------------------------

@@ -14,7 +14,7 @@ import json
 import numpy as np
 
 from . import _lib
-from ._lib import MTP_FP64, MTP_GRADE_FP64, MTP_GRADE_TENSOR, MTP_MIXED, MtpError, check
+from ._lib import MTP_FP64, MTP_GRADE_FP64, MTP_GRADE_TENSOR, MTP_MIXED, MTP_OK, MTP_STATUS_BREAK, MtpError, check
 
 __all__ = [
     "MTP_FP64", "MTP_MIXED", "MTP_GRADE_TENSOR", "MTP_GRADE_FP64", "MtpError", "Potential", "NeighborList", "mtp_basis_info", "mtp_basis_table",
@@ -118,6 +118,12 @@ class Potential:
         n = ctypes.c_int64()
         check(lib.mtp_param_count(h, ctypes.byref(n)))
         self.n_params = n.value
+        self._theta0 = np.concatenate([s, c, x])
+
+    def initial_theta(self, device="cuda"):
+        """The parameter vector [s | c | xi] the potential was loaded with (FP64 tensor)."""
+        import torch
+        return torch.tensor(self._theta0, dtype=torch.float64, device=device)
 
     @classmethod
     def from_dict(cls, pot: dict, check_basis: bool = True):
@@ -408,6 +414,14 @@ def mtp_compute_efv_tangent(potential: Potential, nlist: NeighborList, x, z, cel
     return out
 
 
+def mtp_set_theta(potential: Potential, theta, stream=None) -> None:
+    """Replace the potential's parameters by theta (CUDA FP64 tensor
+    [n_params], layout [s | c | xi]); queued on ``stream``."""
+    import torch
+    check(_lib.load().mtp_set_theta(potential.handle, _dptr(theta, torch.float64, potential.n_params, "theta"),
+                                    _stream_ptr(stream)))
+
+
 def mtp_device_status(potential: Potential, stream=None) -> int:
     """Device-side status since the last check (0 = fine); raises on error."""
     return check(_lib.load().mtp_device_status(potential.handle, _stream_ptr(stream)))
@@ -499,16 +513,43 @@ class MD:
         masses: per species, amu; dt in ps.  rebuild_every: < 0 check the
         displacements every step and rebuild when needed, > 0 rebuild every
         that many steps, 0 never (no synchronisation).  e_pot / e_kin: optional
-        CUDA tensors [n_steps] float64 that receive the energies after each step."""
+        CUDA tensors [n_steps] float64 that receive the energies after each step.
+        Returns MTP_OK, or MTP_STATUS_BREAK when an in-run grade (set_grade)
+        exceeded the break threshold (the run stopped after that step)."""
         import torch
         n = self.n_atoms
         m = _host_d(masses, self._pot.n_species)
-        check(_lib.load().mtp_md_run(
+        return check(_lib.load().mtp_md_run(
             self._pot.handle, self._md, _dptr(x, torch.float64, 3 * n, "x"), _dptr(v, torch.float64, 3 * n, "v"),
             _dptr(z, torch.int32, n, "z"), m.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), float(dt), int(n_steps),
             int(rebuild_every), int(precision), _dptr(forces, torch.float64, 3 * n, "forces"),
             _dptr(e_pot, torch.float64, n_steps, "e_pot") if e_pot is not None else None,
             _dptr(e_kin, torch.float64, n_steps, "e_kin") if e_kin is not None else None, _stream_ptr(stream)))
+
+    def set_grade(self, a_inv, every, tau_sel=2.0, tau_brk=10.0, method=MTP_GRADE_TENSOR, selected=None):
+        """Evaluate the neighbourhood grade every ``every`` steps inside run();
+        ``selected`` (CUDA uint8 [N], optional) accumulates the flags.  a_inv=None turns it off."""
+        import torch
+        m = self._pot.m
+        self._a_inv = a_inv   # kept alive: the library holds the pointer
+        self._selected = selected
+        check(_lib.load().mtp_md_set_grade(
+            self._pot.handle, self._md, _dptr(a_inv, torch.float64, m * m, "a_inv") if a_inv is not None else None,
+            int(every), float(tau_sel), float(tau_brk), int(method),
+            _dptr(selected, torch.uint8, self.n_atoms, "selected") if selected is not None else None))
+
+    def set_barostat(self, p_target_bar, tau_p_ps, bulk_modulus_bar=10.0):
+        """Berendsen NPT (isotropic); tau_p_ps <= 0 turns it off."""
+        check(_lib.load().mtp_md_set_barostat(self._md, float(p_target_bar), float(tau_p_ps), float(bulk_modulus_bar)))
+
+    def info(self) -> dict:
+        st, ev, ns = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+        gm, pr = ctypes.c_double(), ctypes.c_double()
+        cell = np.zeros(9)
+        check(_lib.load().mtp_md_info(self._md, ctypes.byref(st), ctypes.byref(ev), ctypes.byref(gm), ctypes.byref(ns),
+                                      ctypes.byref(pr), cell.ctypes.data_as(ctypes.POINTER(ctypes.c_double))))
+        return {"steps": st.value, "grade_evals": ev.value, "gamma_max_last": gm.value,
+                "n_selected_last": ns.value, "pressure_bar": pr.value, "cell": cell.reshape(3, 3)}
 
     def __del__(self):
         md = getattr(self, "_md", None)
@@ -525,3 +566,15 @@ class _NeighborListView(NeighborList):
 
     def __del__(self):
         self._nl = None
+
+
+PROBE_FP32, PROBE_FP64, PROBE_FP32X2 = 0, 1, 2
+
+
+def mtp_probe_fma(kind=PROBE_FP32, iters=4096, blocks_per_sm=4) -> dict:
+    """Measured FMA throughput of the current device (flop/s and the timed
+    kernel's ms): kind 0 FP32, 1 FP64, 2 packed FP32 pairs."""
+    f = ctypes.c_double()
+    ms = ctypes.c_double()
+    check(_lib.load().mtp_probe_fma(int(kind), int(iters), int(blocks_per_sm), ctypes.byref(f), ctypes.byref(ms)))
+    return {"flops_per_s": f.value, "ms": ms.value}

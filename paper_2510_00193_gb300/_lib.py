@@ -58,6 +58,7 @@ SIGNATURES = {
     "mtp_load_params": (ctypes.c_int, [ctypes.POINTER(ParamsDesc), ctypes.POINTER(_VP)]),
     "mtp_free": (None, [_VP]),
     "mtp_param_count": (ctypes.c_int, [_VP, _P_I64]),
+    "mtp_set_theta": (ctypes.c_int, [_VP, _VP, _VP]),
     "mtp_build_neighbors": (ctypes.c_int, [_VP, _VP, _I64, _P_D, _P_I32, ctypes.POINTER(_VP), _VP]),
     "mtp_nlist_info": (ctypes.c_int, [_VP, _P_I64, _P_I64]),
     "mtp_nlist_copy": (ctypes.c_int, [_VP, _VP, _VP, _VP, _VP]),
@@ -82,8 +83,13 @@ SIGNATURES = {
     "mtp_md_run": (ctypes.c_int, [_VP, _VP, _VP, _VP, _VP, _P_D, ctypes.c_double, _I32, _I32, _I32, _VP, _VP, _VP,
                                   _VP]),
     "mtp_md_free": (None, [_VP]),
+    "mtp_md_set_grade": (ctypes.c_int, [_VP, _VP, _VP, _I32, ctypes.c_double, ctypes.c_double, _I32, _VP]),
+    "mtp_md_set_barostat": (ctypes.c_int, [_VP, ctypes.c_double, ctypes.c_double, ctypes.c_double]),
+    "mtp_md_info": (ctypes.c_int, [_VP, _P_I64, _P_I64, _P_D, _P_I64, _P_D, _P_D]),
     "mtp_device_status": (ctypes.c_int, [_VP, _VP]),
     "mtp_last_error": (ctypes.c_char_p, []),
+    "mtp_probe_fma": (ctypes.c_int, [_I32, _I64, _I32, _P_D, _P_D]),
+    "mtp_set_wait_limit": (ctypes.c_int, [_I64]),
 }
 
 _lib = None

@@ -5,14 +5,15 @@ backward (directional second derivatives from the dual-number kernel), so
 that a force-matching loss can be differentiated with respect to theta.
 
 All arithmetic runs in the CUDA library; these classes only route tensors.
-The parameters themselves live in the Potential handle: theta is the
-autograd stand-in for them (rebuild the Potential after changing them).
+theta drives the potential: the forward pass and the double backward upload
+it into the Potential handle (mtp_set_theta) before they evaluate, so a
+training loop can update theta between steps without rebuilding the handle.
 """
 from __future__ import annotations
 
 import torch
 
-from . import MTP_FP64, mtp_compute_efv, mtp_compute_efv_tangent
+from . import MTP_FP64, mtp_compute_efv, mtp_compute_efv_tangent, mtp_set_theta
 
 
 class MTPEnergy(torch.autograd.Function):
@@ -20,6 +21,7 @@ class MTPEnergy(torch.autograd.Function):
 
     @staticmethod
     def forward(ctx, x, theta, potential, nlist, z, cell, precision):
+        mtp_set_theta(potential, theta.detach().contiguous())
         out = mtp_compute_efv(potential, nlist, x.detach(), z, cell, precision=precision, dtheta=True)
         ctx.save_for_backward(x, theta, out["forces"], out["dtheta"])
         ctx.info = (potential, nlist, z, cell, precision)
@@ -38,18 +40,19 @@ class MTPEnergyGrad(torch.autograd.Function):
 
     @staticmethod
     def forward(ctx, x, theta, g_e, forces, dtheta, potential, nlist, z, cell, precision):
-        ctx.save_for_backward(x, g_e, forces, dtheta)
+        ctx.save_for_backward(x, theta, g_e, forces, dtheta)
         ctx.info = (potential, nlist, z, cell, precision)
         return -forces * g_e, dtheta * g_e
 
     @staticmethod
     def backward(ctx, g_gx, g_gth):
-        x, g_e, forces, dtheta = ctx.saved_tensors
+        x, theta, g_e, forces, dtheta = ctx.saved_tensors
         potential, nlist, z, cell, precision = ctx.info
         if g_gth is not None and bool(torch.any(g_gth != 0)):
             raise NotImplementedError("second derivatives along theta are not provided")
         if g_gx is None:
             return (None,) * 10
+        mtp_set_theta(potential, theta.detach().contiguous())   # the parameters of this graph's forward
         tan = mtp_compute_efv_tangent(potential, nlist, x.detach(), z, cell, g_gx.contiguous(),
                                       precision=precision, force_tan=True)
         grad_x = -tan["force_tan"] * g_e          # g_e H v

@@ -59,16 +59,18 @@ __global__ void batch_fixed_point_kernel(const double* __restrict__ s, const int
   if (i >= n) return;
   const double k = 4294967296.0;
   const double s0 = s[3 * i], s1 = s[3 * i + 1], s2 = s[3 * i + 2];
+  const int zi = z[i];
+  const bool z_ok = zi >= 0 && zi < S;
+  if (!z_ok) atomicCAS(status, 0, MTP_ERR_ARG);
+  out[4 * i + 3] = z_ok ? (long long)zi : 0ll;   // out-of-range species read as 0 (reported above)
   if (!(fabs(s0) < 2147483647.0 && fabs(s1) < 2147483647.0 && fabs(s2) < 2147483647.0)) {
-    atomicCAS(status, 0, MTP_ERR_NONFINITE);
+    atomicCAS(status, 0, MTP_ERR_NONFINITE);   // stored as the origin: no kernel reads undefined coordinates
+    out[4 * i] = out[4 * i + 1] = out[4 * i + 2] = 0ll;
     return;
   }
-  const int zi = z[i];
-  if (zi < 0 || zi >= S) atomicCAS(status, 0, MTP_ERR_ARG);
   out[4 * i] = __double2ll_rn(s0 * k);
   out[4 * i + 1] = __double2ll_rn(s1 * k);
   out[4 * i + 2] = __double2ll_rn(s2 * k);
-  out[4 * i + 3] = (long long)zi;
 }
 
 struct BatchNbrArgs {

@@ -49,7 +49,7 @@ __global__ void __launch_bounds__(256) batch_kernel(const BatchArgs b) {
     R w[6] = {R(0), R(0), R(0), R(0), R(0), R(0)};
     const bool active = (int)threadIdx.x < count;
     if (__any_sync(0xffffffffu, active))   // warp-uniform: whole warps without atoms skip the work
-      efv_atom<LV, R, DTHETA>(a, sm, active ? first + threadIdx.x : first, active, s_cell, e_i, w);
+      efv_atom<LV, R, DTHETA>(a, sm, active ? first + threadIdx.x : first, active, s_cell, nullptr, e_i, w);
     efv_block_flush<LV, R, DTHETA>(sm, e_i, w, b.e_cfg + cfg, b.virial_cfg + (int64_t)cfg * 6,
                                    DTHETA ? b.dtheta_cfg + (int64_t)cfg * b.n_params : nullptr);
     __syncthreads();

@@ -14,6 +14,8 @@
 #pragma once
 #include <cuda_runtime.h>
 
+#include <type_traits>
+
 #include "mtp_internal.cuh"
 #include "mtp_math.cuh"
 
@@ -60,7 +62,7 @@ template <> struct PairGeom<double> {
     l.x = __ldg(a.x + 3 * (int64_t)j);
     l.y = __ldg(a.x + 3 * (int64_t)j + 1);
     l.z = __ldg(a.x + 3 * (int64_t)j + 2);
-    l.species = __ldg(a.z + j);
+    l.species = species_at(a.z, j, a.n_species);
     return l;
   }
   __device__ __forceinline__ void vec(const EfvArgs& a, const Load& l, int32_t img, double& dx, double& dy,
@@ -103,11 +105,13 @@ template <> struct PairGeom<float> {
   };
   long long qx, qy, qz;
   const float* c;    // cell rows of the configuration
+  int32_t ci;        // centre atom (for the FP64 evaluation of close pairs)
   __device__ __forceinline__ void load_centre(const EfvArgs& a, int64_t i, const float* cell) {
     const longlong2 p = *reinterpret_cast<const longlong2*>(a.xq + 4 * i);
     const longlong2 q = *reinterpret_cast<const longlong2*>(a.xq + 4 * i + 2);
     qx = p.x; qy = p.y; qz = q.x;
     c = cell;
+    ci = (int32_t)i;
   }
   __device__ __forceinline__ Load fetch(const EfvArgs& a, int32_t j) const {
     Load l;
@@ -225,6 +229,78 @@ __device__ __forceinline__ void radial(const C* __restrict__ c, int nq, R r, R m
   }
 }
 
+// Pairs closer than R_min on the mixed path.  Below R_min the radial basis is
+// extrapolated: the Chebyshev polynomials are evaluated at xi < -1, where
+// they grow like cosh(k arccosh |xi|) and are steep, so the FP32 rounding of
+// the distance (a few units in the last place) is amplified in f_mu and
+// df_mu/dr, and at such close contacts the pair gradient is a sum of large
+// basis-function terms that cancel (on the 256,000-atom level-20 workload this
+// gave force errors of 0.15 eV/A against FP64 on the atoms of its closest
+// pairs).  These pairs are rare (about 7e-4 per atom there), so for them the
+// pair vector comes from the FP64 positions and the distance, the radial
+// functions, their derivatives and (with WANT_Q) the basis values Q_k are
+// evaluated in FP64 with the FP64 coefficients, then rounded to FP32 once.
+// `cell` holds the FP64 rows of the configuration's cell.  Used by the
+// level-18/20 split kernels; the fused kernels keep FP32 for every pair
+// (an inlined FP64 branch cost them 20% at level 16, where no pair of the
+// 1,024,000-atom workload comes closer than R_min, and 3x on the random
+// gases, where a third of the warp iterations hold a pair between the 1.9 A
+// minimum separation and R_min = 2 A and GB300's FP64 pipe serialises them).
+template <int NMU, bool DERIV, bool WANT_Q>
+__device__ __forceinline__ void close_pair_fp64(const EfvArgs& a, const double* cell, int32_t ci, int32_t j,
+                                                int32_t img, int zi, int zj, float& dx, float& dy, float& dz,
+                                                float& rinv, float* f, float* df, float* q) {
+  int n1, n2, n3;
+  unpack_image(img, n1, n2, n3);
+  const double sx = ((double)n1 * cell[0] + (double)n2 * cell[3]) + (double)n3 * cell[6];
+  const double sy = ((double)n1 * cell[1] + (double)n2 * cell[4]) + (double)n3 * cell[7];
+  const double sz = ((double)n1 * cell[2] + (double)n2 * cell[5]) + (double)n3 * cell[8];
+  const double ex = (a.x[3 * (int64_t)j] + sx) - a.x[3 * (int64_t)ci];
+  const double ey = (a.x[3 * (int64_t)j + 1] + sy) - a.x[3 * (int64_t)ci + 1];
+  const double ez = (a.x[3 * (int64_t)j + 2] + sz) - a.x[3 * (int64_t)ci + 2];
+  const double r = sqrt(fma(ez, ez, fma(ey, ey, ex * ex)));
+  const double ri = 1.0 / r;
+  dx = (float)ex;
+  dy = (float)ey;
+  dz = (float)ez;
+  rinv = (float)ri;
+  const int S = a.n_species, nq = a.n_q;
+  const double x = (r - 0.5 * (a.r_min + a.r_cut)) * (2.0 / (a.r_cut - a.r_min));
+  const double scale = 2.0 / (a.r_cut - a.r_min);
+  const double cut = a.r_cut - r;
+  const double cut2 = cut * cut;
+  double A[NMU], B[NMU];
+  const double* cz = a.radial_d + (int64_t)zi * S + zj;   // c[mu][k][zi][zj] at cz[(mu nq + k) S^2]
+  const int64_t ss = (int64_t)S * S;
+  double t0 = 1.0, t1 = x, d0 = 0.0, d1 = 1.0;
+#pragma unroll
+  for (int mu = 0; mu < NMU; ++mu) {
+    A[mu] = cz[(int64_t)mu * nq * ss];
+    B[mu] = 0.0;
+  }
+  if (WANT_Q) q[0] = (float)cut2;
+  for (int k = 1; k < nq; ++k) {
+    double tk = t1, dk = d1;
+    if (k >= 2) {
+      tk = 2.0 * x * t1 - t0;
+      dk = 2.0 * x * d1 + 2.0 * t1 - d0;
+      t0 = t1; t1 = tk; d0 = d1; d1 = dk;
+    }
+#pragma unroll
+    for (int mu = 0; mu < NMU; ++mu) {
+      const double cc = cz[((int64_t)mu * nq + k) * ss];
+      A[mu] = fma(cc, tk, A[mu]);
+      if (DERIV) B[mu] = fma(cc, dk, B[mu]);
+    }
+    if (WANT_Q) q[k] = (float)(tk * cut2);
+  }
+#pragma unroll
+  for (int mu = 0; mu < NMU; ++mu) {
+    f[mu] = (float)(cut2 * A[mu]);
+    if (DERIV) df[mu] = (float)(scale * cut2 * B[mu] - 2.0 * cut * A[mu]);
+  }
+}
+
 // Byte offset of the FP64 reduction area in the kernel's dynamic shared memory.
 template <class R, int NMU, bool DTHETA>
 __host__ __device__ __forceinline__ size_t efv_red_offset(int SS, int nq, int m) {
@@ -253,7 +329,7 @@ struct EfvShared {
   double* red;
   int* cnt;   // [S]
   int S, SS, nq, cstride, m;
-  R rcut, mid, scale;
+  R rcut, mid, scale, rmin;
 
   __device__ __forceinline__ void setup(const EfvArgs& a, unsigned char* raw) {
     S = a.n_species;
@@ -282,6 +358,7 @@ struct EfvShared {
     }
     for (int t = threadIdx.x; t < m; t += blockDim.x) xi[t] = xi_src[t];
     rcut = R(a.r_cut);
+    rmin = R(a.r_min);
     mid = R(0.5 * (a.r_min + a.r_cut));
     scale = R(2.0 / (a.r_cut - a.r_min));
   }
@@ -296,9 +373,11 @@ struct EfvShared {
 
 // First neighbour sweep: M[c] += f_mu(r_ij) rhat^K for the components of
 // group G (G < 0: all components; G >= 0: the level's component group G).
-template <class LV, class R, bool DTHETA, int G>
+// CLOSE64 (mixed path only): pairs closer than R_min take close_pair_fp64.
+template <class LV, class R, bool DTHETA, int G, bool CLOSE64 = false>
 __device__ __forceinline__ void moment_sweep(const EfvArgs& a, const EfvShared<R, LV::NMU, DTHETA>& sm,
-                                             const PairGeom<R>& geom, int zi, int64_t beg, int64_t end, R* M) {
+                                             const PairGeom<R>& geom, const double* cell64, int zi, int64_t beg,
+                                             int64_t end, R* M) {
   constexpr int NMU = LV::NMU;
   PairStream<R> ps;
   int32_t j, img;
@@ -308,11 +387,20 @@ __device__ __forceinline__ void moment_sweep(const EfvArgs& a, const EfvShared<R
     R dx, dy, dz;
     geom.vec(a, lj, img, dx, dy, dz);
     const R r2 = fmadd(dz, dz, fmadd(dy, dy, dx * dx));
-    const R rinv = rsqrt_r(r2);
+    R rinv = rsqrt_r(r2);
     const R r = r2 * rinv;
     R f[NMU];
-    radial<R, NMU, false, false>(sm.c + (zi * sm.S + lj.species) * sm.cstride, sm.nq, r, sm.mid, sm.scale, sm.rcut, f,
-                                 nullptr, nullptr);
+    if constexpr (CLOSE64 && std::is_same<R, float>::value) {
+      if (r < sm.rmin)
+        close_pair_fp64<NMU, false, false>(a, cell64, geom.ci, j, img, zi, lj.species, dx, dy,
+                                           dz, rinv, f, nullptr, nullptr);
+      else
+        radial<R, NMU, false, false>(sm.c + (zi * sm.S + lj.species) * sm.cstride, sm.nq, r, sm.mid, sm.scale,
+                                     sm.rcut, f, nullptr, nullptr);
+    } else {
+      radial<R, NMU, false, false>(sm.c + (zi * sm.S + lj.species) * sm.cstride, sm.nq, r, sm.mid, sm.scale, sm.rcut,
+                                   f, nullptr, nullptr);
+    }
     if constexpr (G < 0) LV::template moments<R>(M, f, dx * rinv, dy * rinv, dz * rinv);
     else LV::template moments_group<G, R>(M, f, dx * rinv, dy * rinv, dz * rinv);
   }
@@ -322,9 +410,11 @@ __device__ __forceinline__ void moment_sweep(const EfvArgs& a, const EfvShared<R
 // g_ij = dE_i/dr_ij from D (the group's share), F_i += g, F_j -= g,
 // W -= sym(g (x) r_ij) and, with DTHETA, the group's radial functions'
 // dE/dc terms Q_k(r) S_mu into acc (own_acc) or the shared accumulators.
-template <class LV, class R, bool DTHETA, int G>
+// CLOSE64 as in moment_sweep.
+template <class LV, class R, bool DTHETA, int G, bool CLOSE64 = false>
 __device__ __forceinline__ void adjoint_sweep(const EfvArgs& a, const EfvShared<R, LV::NMU, DTHETA>& sm,
-                                              const PairGeom<R>& geom, int zi, int64_t beg, int64_t end,
+                                              const PairGeom<R>& geom, const double* cell64, int zi, int64_t beg,
+                                              int64_t end,
                                               const R* D, R& fx, R& fy, R& fz, R* w, R* acc, bool own_acc) {
   constexpr int NMU = LV::NMU;
   PairStream<R> ps;
@@ -336,10 +426,20 @@ __device__ __forceinline__ void adjoint_sweep(const EfvArgs& a, const EfvShared<
     R dx, dy, dz;
     geom.vec(a, lj, img, dx, dy, dz);
     const R r2 = fmadd(dz, dz, fmadd(dy, dy, dx * dx));
-    const R rinv = rsqrt_r(r2);
+    R rinv = rsqrt_r(r2);
     const R r = r2 * rinv;
     R f[NMU], df[NMU], q[DTHETA ? kMaxQ : 1];
-    radial<R, NMU, true, DTHETA>(sm.c + (zi * sm.S + zj) * sm.cstride, sm.nq, r, sm.mid, sm.scale, sm.rcut, f, df, q);
+    if constexpr (CLOSE64 && std::is_same<R, float>::value) {
+      if (r < sm.rmin)
+        close_pair_fp64<NMU, true, DTHETA>(a, cell64, geom.ci, j, img, zi, zj, dx, dy, dz, rinv,
+                                           f, df, q);
+      else
+        radial<R, NMU, true, DTHETA>(sm.c + (zi * sm.S + zj) * sm.cstride, sm.nq, r, sm.mid, sm.scale, sm.rcut, f, df,
+                                     q);
+    } else {
+      radial<R, NMU, true, DTHETA>(sm.c + (zi * sm.S + zj) * sm.cstride, sm.nq, r, sm.mid, sm.scale, sm.rcut, f, df,
+                                   q);
+    }
     R gx, gy, gz, Smu[NMU];
     if constexpr (G < 0)
       LV::template pair_adjoint<R>(D, f, df, dx * rinv, dy * rinv, dz * rinv, rinv, gx, gy, gz, Smu);
@@ -385,7 +485,8 @@ __device__ __forceinline__ void adjoint_sweep(const EfvArgs& a, const EfvShared<
 // Everything one centre atom contributes: its site energy (also stored in
 // e_atom), its force terms (scattered), its virial terms (w) and, with
 // DTHETA, its basis values and radial-coefficient gradient (shared
-// accumulators).  `cell` holds the rows of its configuration's cell.
+// accumulators).  `cell` holds the rows of its configuration's cell in the
+// working precision, `cell64` in FP64.
 // Every lane of the warp calls this (the basis values are summed across the
 // warp right after the contraction, which frees their registers for the
 // second sweep): a lane without an atom passes active = false and a valid
@@ -397,31 +498,31 @@ __device__ __forceinline__ void adjoint_sweep(const EfvArgs& a, const EfvShared<
 // vectors meet the interpreter once per atom.
 template <class LV, class R, bool DTHETA>
 __device__ __forceinline__ void efv_atom(const EfvArgs& a, const EfvShared<R, LV::NMU, DTHETA>& sm, int64_t i,
-                                         bool active, const R* cell, double& e_i, R* w) {
+                                         bool active, const R* cell, const double* cell64, double& e_i, R* w) {
   constexpr int NMU = LV::NMU;
   static_assert(LV::NGROUPS == 1 || LV::NGROUPS == 2, "one or two component groups");
   PairGeom<R> geom;
   geom.load_centre(a, i, cell);
-  const int zi = __ldg(a.z + i);
+  const int zi = species_at(a.z, i, a.n_species);
   const int64_t beg = active ? __ldg(a.offsets + i) : 0, end = active ? __ldg(a.offsets + i + 1) : 0;
   R M[LV::NCOMP];
 #pragma unroll
   for (int c = 0; c < LV::NCOMP; ++c) M[c] = R(0);
   if constexpr (LV::NGROUPS == 1) {
-    moment_sweep<LV, R, DTHETA, -1>(a, sm, geom, zi, beg, end, M);
+    moment_sweep<LV, R, DTHETA, -1>(a, sm, geom, cell64, zi, beg, end, M);
   } else {
     {
       R Mg[LV::NCOMP];
 #pragma unroll
       for (int c = 0; c < LV::NCOMP; ++c) Mg[c] = R(0);
-      moment_sweep<LV, R, DTHETA, 0>(a, sm, geom, zi, beg, end, Mg);
+      moment_sweep<LV, R, DTHETA, 0>(a, sm, geom, cell64, zi, beg, end, Mg);
       LV::template store_group<0, R>(Mg, M, 1);
     }
     {
       R Mg[LV::NCOMP];
 #pragma unroll
       for (int c = 0; c < LV::NCOMP; ++c) Mg[c] = R(0);
-      moment_sweep<LV, R, DTHETA, 1>(a, sm, geom, zi, beg, end, Mg);
+      moment_sweep<LV, R, DTHETA, 1>(a, sm, geom, cell64, zi, beg, end, Mg);
       LV::template store_group<1, R>(Mg, M, 1);
     }
   }
@@ -454,17 +555,17 @@ __device__ __forceinline__ void efv_atom(const EfvArgs& a, const EfvShared<R, LV
     for (int t = 0; t < sm.S * NMU * sm.nq; ++t) acc[t] = R(0);
   }
   if constexpr (LV::NGROUPS == 1) {
-    adjoint_sweep<LV, R, DTHETA, -1>(a, sm, geom, zi, beg, end, D, fx, fy, fz, w, acc, own_acc);
+    adjoint_sweep<LV, R, DTHETA, -1>(a, sm, geom, cell64, zi, beg, end, D, fx, fy, fz, w, acc, own_acc);
   } else {
     {
       R Dg[LV::NCOMP];
       LV::template load_group<0, R>(D, 1, Dg);
-      adjoint_sweep<LV, R, DTHETA, 0>(a, sm, geom, zi, beg, end, Dg, fx, fy, fz, w, acc, own_acc);
+      adjoint_sweep<LV, R, DTHETA, 0>(a, sm, geom, cell64, zi, beg, end, Dg, fx, fy, fz, w, acc, own_acc);
     }
     {
       R Dg[LV::NCOMP];
       LV::template load_group<1, R>(D, 1, Dg);
-      adjoint_sweep<LV, R, DTHETA, 1>(a, sm, geom, zi, beg, end, Dg, fx, fy, fz, w, acc, own_acc);
+      adjoint_sweep<LV, R, DTHETA, 1>(a, sm, geom, cell64, zi, beg, end, Dg, fx, fy, fz, w, acc, own_acc);
     }
   }
   if (!active) return;
@@ -535,7 +636,7 @@ __global__ void __launch_bounds__(kEfvThreads) efv_kernel(const EfvArgs a) {
   R w[6] = {R(0), R(0), R(0), R(0), R(0), R(0)};
   const bool active = i < a.atom_end;
   if (__any_sync(0xffffffffu, active))   // warp-uniform: whole warps without atoms skip the work
-    efv_atom<LV, R, DTHETA>(a, sm, active ? i : a.atom_begin, active, cell_of<R>(a), e_i, w);
+    efv_atom<LV, R, DTHETA>(a, sm, active ? i : a.atom_begin, active, cell_of<R>(a), a.cell, e_i, w);
   efv_block_flush<LV, R, DTHETA>(sm, e_i, w, a.e_total, a.virial, a.dtheta);
 }
 
@@ -558,21 +659,21 @@ __global__ void __launch_bounds__(kEfvThreads) split_moments_kernel(const EfvArg
   const int64_t i = a.atom_begin + (active ? t : 0);
   PairGeom<R> geom;
   geom.load_centre(a, i, cell_of<R>(a));
-  const int zi = __ldg(a.z + i);
+  const int zi = species_at(a.z, i, a.n_species);
   const int64_t beg = active ? __ldg(a.offsets + i) : 0, end = active ? __ldg(a.offsets + i + 1) : 0;
   R* buf = static_cast<R*>(a.mbuf) + (active ? t : 0);
   {
     R Mg[LV::NCOMP];
 #pragma unroll
     for (int c = 0; c < LV::NCOMP; ++c) Mg[c] = R(0);
-    moment_sweep<LV, R, false, 0>(a, sm, geom, zi, beg, end, Mg);
+    moment_sweep<LV, R, false, 0, true>(a, sm, geom, a.cell, zi, beg, end, Mg);
     if (active) LV::template store_group<0, R>(Mg, buf, n);
   }
   {
     R Mg[LV::NCOMP];
 #pragma unroll
     for (int c = 0; c < LV::NCOMP; ++c) Mg[c] = R(0);
-    moment_sweep<LV, R, false, 1>(a, sm, geom, zi, beg, end, Mg);
+    moment_sweep<LV, R, false, 1, true>(a, sm, geom, a.cell, zi, beg, end, Mg);
     if (active) LV::template store_group<1, R>(Mg, buf, n);
   }
 }
@@ -608,7 +709,7 @@ __global__ void __launch_bounds__(kEfvThreads) split_contract_kernel(const EfvAr
     }
     if (active) {
       const int64_t i = a.atom_begin + t;
-      const int zi = __ldg(a.z + i);
+      const int zi = species_at(a.z, i, a.n_species);
       e_i = a.species_energy[zi] + (double)ei;
       a.e_atom[i] = e_i;
       if (!isfinite(e_i)) flag_status(a.status, MTP_ERR_NONFINITE);
@@ -634,7 +735,7 @@ __global__ void __launch_bounds__(kEfvThreads) split_adjoint_kernel(const EfvArg
     const int64_t i = a.atom_begin + (active ? t : 0);
     PairGeom<R> geom;
     geom.load_centre(a, i, cell_of<R>(a));
-    const int zi = __ldg(a.z + i);
+    const int zi = species_at(a.z, i, a.n_species);
     const int64_t beg = active ? __ldg(a.offsets + i) : 0, end = active ? __ldg(a.offsets + i + 1) : 0;
     const R* buf = static_cast<const R*>(a.mbuf) + (size_t)LV::NCOMP * n + (active ? t : 0);
     R fx = R(0), fy = R(0), fz = R(0);
@@ -647,12 +748,12 @@ __global__ void __launch_bounds__(kEfvThreads) split_adjoint_kernel(const EfvArg
     {
       R Dg[LV::NCOMP];
       LV::template load_group<0, R>(buf, n, Dg);
-      adjoint_sweep<LV, R, DTHETA, 0>(a, sm, geom, zi, beg, end, Dg, fx, fy, fz, w, acc, own_acc);
+      adjoint_sweep<LV, R, DTHETA, 0, true>(a, sm, geom, a.cell, zi, beg, end, Dg, fx, fy, fz, w, acc, own_acc);
     }
     {
       R Dg[LV::NCOMP];
       LV::template load_group<1, R>(buf, n, Dg);
-      adjoint_sweep<LV, R, DTHETA, 1>(a, sm, geom, zi, beg, end, Dg, fx, fy, fz, w, acc, own_acc);
+      adjoint_sweep<LV, R, DTHETA, 1, true>(a, sm, geom, a.cell, zi, beg, end, Dg, fx, fy, fz, w, acc, own_acc);
     }
     if (active) {
       if (own_acc) {

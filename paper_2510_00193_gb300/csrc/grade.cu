@@ -349,8 +349,27 @@ extern "C" int mtp_grade_tc_selftest(const uint16_t* xs, const uint16_t* ys, con
     return MTP_ERR_ARG;
   }
   cudaStream_t s = (cudaStream_t)stream;
-  int rc = tc_gemm(xs, ys, fexp, erow, n_rows, reinterpret_cast<unsigned long long*>(gamma_bits), nullptr, acc, s);
+  int* status = nullptr;
+  MTP_TRY_CUDA(cudaMalloc(&status, sizeof(int)));
+  int st = 0;
+  cudaError_t e = cudaMemsetAsync(status, 0, sizeof(int), s);
+  int rc = e == cudaSuccess ? tc_gemm(xs, ys, fexp, erow, n_rows, reinterpret_cast<unsigned long long*>(gamma_bits),
+                                      status, acc, s)
+                            : MTP_ERR_CUDA;
+  if (rc == MTP_OK) {
+    e = cudaMemcpyAsync(&st, status, sizeof(int), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) {
+      set_error("mtp_grade_tc_selftest: %s", cudaGetErrorString(e));
+      rc = MTP_ERR_CUDA;
+    }
+  }
+  cudaFree(status);
   if (rc != MTP_OK) return rc;
-  MTP_TRY_CUDA(cudaStreamSynchronize(s));
+  if (st != 0) {
+    set_error(st == MTP_ERR_TIMEOUT ? "mtp_grade_tc_selftest: a device-side wait gave up"
+                                    : "mtp_grade_tc_selftest: device status %d", st);
+    return st;
+  }
   return MTP_OK;
 }

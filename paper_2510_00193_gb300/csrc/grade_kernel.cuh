@@ -44,7 +44,7 @@ __global__ void __launch_bounds__(kRowsThreads) basis_rows_kernel(const EfvArgs 
     const int64_t i = list ? (int64_t)list[r] : a.atom_begin + r;
     PairGeom<R> geom;
     geom.load_centre(a, i, a.cell);
-    const int zi = __ldg(a.z + i);
+    const int zi = species_at(a.z, i, a.n_species);
     R M[LV::NCOMP];
 #pragma unroll
     for (int c = 0; c < LV::NCOMP; ++c) M[c] = R(0);

@@ -69,6 +69,10 @@ constexpr int kXBufs = 2;
 constexpr int kTcThreads = 192;
 constexpr uint32_t kTmemCols = 512;
 constexpr uint64_t kTcTimeoutNs = 1000000000ull;  // 1 s per wait
+// Limit of the pipeline waits (producer, MMA issuer, epilogue); the drain
+// waits at the end (for copies and MMAs already issued) always allow
+// kTcTimeoutNs, so a block never exits with work of its own in flight.
+static uint64_t g_tc_wait_ns = kTcTimeoutNs;
 
 // X slice layout (BF16 elements) inside one [128 rows][128 K] tile:
 // element (i, j) at (j / 8) * 1024 + (i / 8) * 64 + (i % 8) * 8 + j % 8,
@@ -280,6 +284,7 @@ struct TcGemmArgs {
   unsigned long long* gbits;   // [n_rows], zeroed: atomicMax of gamma bits over the two halves
   int* status;
   float* dbg;                  // nullable: raw accumulators [n_tiles*128][2][7][64]
+  uint64_t wait_ns;            // limit of each pipeline wait
 };
 
 __global__ void __launch_bounds__(kTcThreads, 1) tc_grade_kernel(const TcGemmArgs p) {
@@ -334,7 +339,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_grade_kernel(const TcGemmArg
         for (int s = 0; s < kTcS; ++s, ++it) {
           const int buf = it & 1;
           const uint32_t ph = (uint32_t)(it >> 1) & 1u;
-          if (!tc::mbar_wait(b_xempty0 + 8 * buf, ph ^ 1u, abort_flag, kTcTimeoutNs)) {
+          if (!tc::mbar_wait(b_xempty0 + 8 * buf, ph ^ 1u, abort_flag, p.wait_ns)) {
             ok = false;
             break;
           }
@@ -360,11 +365,11 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_grade_kernel(const TcGemmArg
     if (lane == 0) {
       // ---- MMA issuer ----
       constexpr uint32_t idesc = tc::idesc_bf16_f32(kTcM, kTcN);
-      bool ok = tc::mbar_wait(b_yfull, 0u, abort_flag, kTcTimeoutNs);
+      bool ok = tc::mbar_wait(b_yfull, 0u, abort_flag, p.wait_ns);
       tc::fence_after_sync();
       int it = 0, tcount = 0;
       for (int tile = cta; ok && tile < p.n_tiles; tile += n_cta, ++tcount) {
-        if (!tc::mbar_wait(b_accempty, ((uint32_t)tcount & 1u) ^ 1u, abort_flag, kTcTimeoutNs)) {
+        if (!tc::mbar_wait(b_accempty, ((uint32_t)tcount & 1u) ^ 1u, abort_flag, p.wait_ns)) {
           ok = false;
           break;
         }
@@ -372,7 +377,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_grade_kernel(const TcGemmArg
         for (int s = 0; s < kTcS; ++s, ++it) {
           const int buf = it & 1;
           const uint32_t ph = (uint32_t)(it >> 1) & 1u;
-          if (!tc::mbar_wait(b_xfull0 + 8 * buf, ph, abort_flag, kTcTimeoutNs)) {
+          if (!tc::mbar_wait(b_xfull0 + 8 * buf, ph, abort_flag, p.wait_ns)) {
             ok = false;
             break;
           }
@@ -408,7 +413,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_grade_kernel(const TcGemmArg
     const uint32_t lane_base = tmem + ((uint32_t)(q * 32) << 16);
     int tcount = 0;
     for (int tile = cta; tile < p.n_tiles; tile += n_cta, ++tcount) {
-      if (!tc::mbar_wait(b_accfull, (uint32_t)tcount & 1u, abort_flag, kTcTimeoutNs)) {
+      if (!tc::mbar_wait(b_accfull, (uint32_t)tcount & 1u, abort_flag, p.wait_ns)) {
         *abort_flag = 1;
         set_status(p.status, MTP_ERR_TIMEOUT);
         break;
@@ -584,6 +589,7 @@ int tc_gemm(const uint16_t* xs, const uint16_t* ys, const int* fexp, const int* 
   p.gbits = gbits;
   p.status = status;
   p.dbg = dbg;
+  p.wait_ns = g_tc_wait_ns;
   const int per_half = (int)std::min<int64_t>(tiles, std::max(1, sm_count() / 2));
   tc_grade_kernel<<<2 * per_half, kTcThreads, kSmAlloc, s>>>(p);
   MTP_TC_CHECK("tc_grade_kernel");
@@ -601,3 +607,8 @@ int tc_finalize(const unsigned long long* gbits, int64_t n, const int* erow, con
 }
 
 }  // namespace mtp
+
+extern "C" int mtp_set_wait_limit(int64_t ns) {
+  mtp::g_tc_wait_ns = ns < 0 ? mtp::kTcTimeoutNs : (uint64_t)ns;
+  return MTP_OK;
+}

@@ -30,8 +30,9 @@ namespace mtp {
 int build_neighbors(mtp_nlist* nl, const double* x, int64_t n, const double* cell, const int32_t* pbc, double r_cut,
                     cudaStream_t stream);
 
-// LAMMPS metal units: 1 amu A^2 / ps^2 = 1.0364269e-4 eV.
+// LAMMPS metal units: 1 amu A^2 / ps^2 = 1.0364269e-4 eV; 1 eV/A^3 = 1.602176634e6 bar.
 constexpr double kMvv2e = 1.0364269e-4;
+constexpr double kEvA3ToBar = 1.602176634e6;
 
 struct MdMass {
   double inv_m[kMaxSpecies];   // 1 / (m kMvv2e): eV/A -> A/ps^2
@@ -52,7 +53,7 @@ __global__ void md_kick_drift_kernel(double* __restrict__ x, double* __restrict_
                                      int* __restrict__ flags) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
-  const double a = mm.inv_m[z[i]] * 0.5 * dt;
+  const double a = mm.inv_m[min(max(z[i], 0), kMaxSpecies - 1)] * 0.5 * dt;   // species checked by the force pass
   double p[3];
   double d2 = 0.0;
 #pragma unroll
@@ -176,7 +177,7 @@ __global__ void md_kick_kernel(double* __restrict__ v, const double* __restrict_
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   double ke = 0.0;
   if (i < n) {
-    const int zi = z[i];
+    const int zi = min(max(z[i], 0), kMaxSpecies - 1);   // species checked by the force pass
     const double a = mm.inv_m[zi] * 0.5 * dt;
     double vv = 0.0;
 #pragma unroll
@@ -201,6 +202,28 @@ __global__ void md_kick_kernel(double* __restrict__ v, const double* __restrict_
   }
 }
 
+// Isotropic cell scaling of the Berendsen barostat: x *= mu and the
+// reference positions of the skin list too (the displacement check then
+// measures the motion relative to the affinely scaled build positions).
+__global__ void md_scale_kernel(double* __restrict__ x, double* __restrict__ xref, double mu, int64_t n3) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n3) return;
+  x[t] *= mu;
+  xref[t] *= mu;
+}
+
+// Selection record of the in-run grade: selected[i] |= flags[i] (bit 0
+// above the selection threshold, bit 1 above the break threshold at some
+// evaluation) and counts[0] += atoms above the selection threshold now.
+__global__ void md_select_kernel(const uint8_t* __restrict__ flags, int64_t n, uint8_t* __restrict__ selected,
+                                 unsigned long long* __restrict__ count) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const bool sel = i < n && (flags[i] & 1u);
+  if (i < n && selected) selected[i] |= flags[i];
+  const unsigned b = __ballot_sync(0xffffffffu, sel);
+  if ((threadIdx.x & 31) == 0 && b) atomicAdd(count, (unsigned long long)__popc(b));
+}
+
 }  // namespace mtp
 
 struct mtp_md {
@@ -220,6 +243,20 @@ struct mtp_md {
   size_t scan_bytes = 0;
   mtp::DevBuf e_atom, small;        // site energies [N]; virial [6], E_pot [1], flags [1]
   mtp::MdFilterGeom geom;
+  int64_t steps_total = 0;          // steps run since creation
+  double scale_since_build = 1.0;   // product of barostat scale factors since the last skin-list build
+  // in-run extrapolation grade (mtp_md_set_grade)
+  const double* a_inv = nullptr;
+  int32_t grade_every = 0, grade_method = 0;
+  double tau_sel = 0, tau_brk = 0;
+  uint8_t* selected = nullptr;
+  mtp::DevBuf gamma, flags, sel_count;
+  int64_t grade_evals = 0, n_selected_last = 0;
+  double gamma_max_last = 0.0;
+  // Berendsen barostat (mtp_md_set_barostat)
+  double p_target = 0, tau_p = 0, modulus = 10.0;
+  double pressure_last = 0.0;
+  double bulk_modulus() const { return modulus; }
 };
 
 namespace {
@@ -228,6 +265,24 @@ using mtp::set_error;
 
 void free_nlist_only(mtp_nlist* nl) {
   if (nl) mtp_free_nlist(nl);
+}
+
+// Cell-dependent parts of the filter geometry (the neighbour-list image
+// shifts are n.H with the current H).
+void md_set_cell(mtp_md* md, const double* cell) {
+  mtp::MdFilterGeom& g = md->geom;
+  for (int k = 0; k < 9; ++k) {
+    md->cell[k] = cell[k];
+    g.cell[k] = cell[k];
+    g.cellf[k] = (float)cell[k];
+  }
+  for (int k = 0; k < 3; ++k) {
+    double hm = 0.0;
+    for (int c = 0; c < 3; ++c) hm = std::max(hm, std::fabs(cell[3 * k + c]));
+    g.hmax[k] = (float)(hm * (1.0 + 1e-6));
+  }
+  if (md->exact)
+    for (int k = 0; k < 9; ++k) md->exact->cell[k] = cell[k];
 }
 
 int md_filter(mtp_md* md, const double* x, cudaStream_t s) {
@@ -287,6 +342,7 @@ int md_rebuild(mtp_handle* h, mtp_md* md, const double* x, cudaStream_t s) {
   MTP_TRY_CUDA(cudaMemsetAsync(dflags, 0, sizeof(int), s));
   md->since_build = 0;
   md->rebuilds += 1;
+  md->scale_since_build = 1.0;
   (void)h;
   return md_filter(md, x, s);
 }
@@ -332,18 +388,9 @@ int mtp_md_create(mtp_handle* h, const double* x, int64_t n, const double* cell,
   md->n_atoms = n;
   md->skin = skin;
   md->r_cut = h->r_cut;
-  for (int k = 0; k < 9; ++k) md->cell[k] = cell[k];
   for (int k = 0; k < 3; ++k) md->pbc[k] = pbc[k] ? 1 : 0;
+  md_set_cell(md, cell);
   MdFilterGeom& g = md->geom;
-  for (int k = 0; k < 9; ++k) {
-    g.cell[k] = cell[k];
-    g.cellf[k] = (float)cell[k];
-  }
-  for (int k = 0; k < 3; ++k) {
-    double hm = 0.0;
-    for (int c = 0; c < 3; ++c) hm = std::max(hm, std::fabs(cell[3 * k + c]));
-    g.hmax[k] = (float)(hm * (1.0 + 1e-6));
-  }
   g.rc2 = h->r_cut * h->r_cut;
   g.rc2_lo = g.rc2_hi = (float)g.rc2;
   if ((double)g.rc2_lo > g.rc2) g.rc2_lo = std::nextafter(g.rc2_lo, 0.0f);
@@ -362,7 +409,7 @@ int mtp_md_create(mtp_handle* h, const double* x, int64_t n, const double* cell,
   if ((rc = md->xref.ensure(sizeof(double) * 3 * n1)) != MTP_OK || (rc = md->xf.ensure(sizeof(float4) * n1)) != MTP_OK ||
       (rc = md->counts.ensure(((sizeof(int64_t) * (n1 + 1) + 255) & ~size_t(255)) + scan + 256)) != MTP_OK ||
       (rc = md->e_atom.ensure(sizeof(double) * n1)) != MTP_OK ||
-      (rc = md->small.ensure(sizeof(double) * 8)) != MTP_OK) {
+      (rc = md->small.ensure(sizeof(double) * 12)) != MTP_OK) {
     mtp_md_free(md);
     return rc;
   }
@@ -447,11 +494,18 @@ int mtp_md_run(mtp_handle* h, mtp_md* md, double* x, double* v, const int32_t* z
   cudaStream_t s = (cudaStream_t)stream;
   const int64_t n = md->n_atoms;
   const unsigned blocks = (unsigned)((n + 255) / 256);
-  const double half_skin2 = 0.25 * md->skin * md->skin;
   double* small = md->small.as<double>();
   int* dflags = reinterpret_cast<int*>(small + 7);
+  const bool npt = md->tau_p > 0.0;
+  const bool graded = md->a_inv && md->grade_every > 0;
   int rc;
   for (int32_t step = 0; step < n_steps; ++step) {
+    // half the skin, less what the barostat has compressed the cell by since
+    // the last build: a pair beyond R_cut + skin then was at least
+    // s (R_cut + skin) - 2 max|dx| away now (s the scale factor since the build)
+    const double reach = md->scale_since_build * (md->r_cut + md->skin) - md->r_cut;
+    const double half_skin = reach > 0.0 ? 0.5 * reach : 0.0;
+    const double half_skin2 = half_skin * half_skin;
     if (rebuild_every > 0 && md->since_build >= rebuild_every) {
       int flags = 0;
       if ((rc = md_read_flags(md, s, &flags)) != MTP_OK) return rc;
@@ -478,15 +532,138 @@ int mtp_md_run(mtp_handle* h, mtp_md* md, double* x, double* v, const int32_t* z
     rc = mtp_compute_efv(h, md->exact, x, z, n, md->cell, precision, 0, md->e_atom.as<double>(), forces, small, ep,
                          nullptr, stream);
     if (rc != MTP_OK) return rc;
-    double* ek = e_kin ? e_kin + step : nullptr;
+    double* ek = e_kin ? e_kin + step : (npt ? small + 8 : nullptr);
     if (ek) MTP_TRY_CUDA(cudaMemsetAsync(ek, 0, sizeof(double), s));
     if (n > 0) {
       md_kick_kernel<<<blocks, 256, 0, s>>>(v, forces, z, mm, dt, n, ek);
       MTP_TRY_CUDA(cudaGetLastError());
     }
     md->since_build += 1;
+    md->steps_total += 1;
+    bool stop = false;
+    if (graded && md->steps_total % md->grade_every == 0) {
+      // extrapolation grade of this step's configuration (the positions and
+      // exact list the forces were computed with), before any cell scaling
+      double gmax = 0.0;
+      rc = mtp_compute_grade(h, md->exact, x, z, n, md->cell, md->a_inv, nullptr, md->tau_sel, md->tau_brk, 0,
+                             md->grade_method, md->gamma.as<double>(), md->flags.as<uint8_t>(), &gmax, nullptr,
+                             nullptr, nullptr, stream);
+      if (rc < 0) return rc;
+      stop = rc == MTP_STATUS_BREAK;
+      unsigned long long* cnt = md->sel_count.as<unsigned long long>();
+      unsigned long long hc = 0;
+      MTP_TRY_CUDA(cudaMemsetAsync(cnt, 0, sizeof(unsigned long long), s));
+      if (n > 0) {
+        md_select_kernel<<<blocks, 256, 0, s>>>(md->flags.as<uint8_t>(), n, md->selected, cnt);
+        MTP_TRY_CUDA(cudaGetLastError());
+      }
+      MTP_TRY_CUDA(cudaMemcpyAsync(&hc, cnt, sizeof(hc), cudaMemcpyDeviceToHost, s));
+      MTP_TRY_CUDA(cudaStreamSynchronize(s));
+      md->grade_evals += 1;
+      md->gamma_max_last = gmax;
+      md->n_selected_last = (int64_t)hc;
+    }
+    if (npt) {
+      // Berendsen barostat, isotropic: P = (2 E_kin + tr W) / (3 V), then
+      // x, the reference positions and the cell scale by
+      // mu = (1 - dt / tau_p (P_target - P) / B)^(1/3)
+      double hv[9];
+      MTP_TRY_CUDA(cudaMemcpyAsync(hv, small, sizeof(double) * 9, cudaMemcpyDeviceToHost, s));
+      MTP_TRY_CUDA(cudaStreamSynchronize(s));
+      const double* H = md->cell;
+      const double vol = std::fabs(H[0] * (H[4] * H[8] - H[5] * H[7]) - H[1] * (H[3] * H[8] - H[5] * H[6]) +
+                                   H[2] * (H[3] * H[7] - H[4] * H[6]));
+      const double p_bar = (2.0 * hv[8] + hv[0] + hv[1] + hv[2]) / (3.0 * vol) * kEvA3ToBar;
+      md->pressure_last = p_bar;
+      const double mu3 = 1.0 - dt / md->tau_p * (md->p_target - p_bar) / md->bulk_modulus();
+      if (!(mu3 > 0.0) || !std::isfinite(mu3)) {
+        set_error("mtp_md_run: barostat scale factor^3 = %g (pressure %g bar); use a longer tau_p", mu3, p_bar);
+        return MTP_ERR_NONFINITE;
+      }
+      const double mu = std::cbrt(mu3);
+      double hn[9];
+      for (int k = 0; k < 9; ++k) hn[k] = H[k] * mu;
+      md_set_cell(md, hn);
+      md->scale_since_build *= mu;
+      if (n > 0) {
+        md_scale_kernel<<<(unsigned)((3 * n + 255) / 256), 256, 0, s>>>(x, md->xref.as<double>(), mu, 3 * n);
+        MTP_TRY_CUDA(cudaGetLastError());
+      }
+    }
+    if (stop) return MTP_STATUS_BREAK;
   }
   if (rebuild_every > 0) return mtp_md_status(md, nullptr, nullptr, stream);
+  return MTP_OK;
+}
+
+int mtp_md_set_grade(mtp_handle* h, mtp_md* md, const double* a_inv_dev, int32_t every, double tau_sel,
+                     double tau_brk, int32_t method, uint8_t* selected_dev) {
+  using namespace mtp;
+  if (!h || !md) {
+    set_error("mtp_md_set_grade: invalid argument");
+    return MTP_ERR_ARG;
+  }
+  if (!a_inv_dev || every <= 0) {   // off
+    md->a_inv = nullptr;
+    md->grade_every = 0;
+    md->selected = nullptr;
+    return MTP_OK;
+  }
+  if (!(tau_sel > 0.0) || !(tau_brk >= tau_sel)) {
+    set_error("mtp_md_set_grade: thresholds must satisfy 0 < tau_sel <= tau_brk");
+    return MTP_ERR_ARG;
+  }
+  if (method != MTP_GRADE_TENSOR && method != MTP_GRADE_FP64) {
+    set_error("mtp_md_set_grade: unknown method %d", (int)method);
+    return MTP_ERR_ARG;
+  }
+  const int64_t n1 = std::max<int64_t>(md->n_atoms, 1);
+  int rc;
+  if ((rc = md->gamma.ensure(sizeof(double) * n1)) != MTP_OK || (rc = md->flags.ensure(n1)) != MTP_OK ||
+      (rc = md->sel_count.ensure(sizeof(unsigned long long))) != MTP_OK)
+    return rc;
+  md->a_inv = a_inv_dev;
+  md->grade_every = every;
+  md->tau_sel = tau_sel;
+  md->tau_brk = tau_brk;
+  md->grade_method = method;
+  md->selected = selected_dev;
+  return MTP_OK;
+}
+
+int mtp_md_set_barostat(mtp_md* md, double p_target_bar, double tau_p_ps, double bulk_modulus_bar) {
+  if (!md) {
+    mtp::set_error("mtp_md_set_barostat: invalid argument");
+    return MTP_ERR_ARG;
+  }
+  if (!(tau_p_ps > 0.0)) {   // off
+    md->tau_p = 0.0;
+    return MTP_OK;
+  }
+  if (!std::isfinite(p_target_bar) || !std::isfinite(tau_p_ps) || !(bulk_modulus_bar > 0.0) ||
+      !std::isfinite(bulk_modulus_bar)) {
+    mtp::set_error("mtp_md_set_barostat: need finite p_target, tau_p > 0 and bulk modulus > 0");
+    return MTP_ERR_ARG;
+  }
+  md->p_target = p_target_bar;
+  md->tau_p = tau_p_ps;
+  md->modulus = bulk_modulus_bar;
+  return MTP_OK;
+}
+
+int mtp_md_info(const mtp_md* md, int64_t* steps_total, int64_t* grade_evals, double* gamma_max_last,
+                int64_t* n_selected_last, double* pressure_last_bar, double* cell) {
+  if (!md) {
+    mtp::set_error("mtp_md_info: invalid argument");
+    return MTP_ERR_ARG;
+  }
+  if (steps_total) *steps_total = md->steps_total;
+  if (grade_evals) *grade_evals = md->grade_evals;
+  if (gamma_max_last) *gamma_max_last = md->gamma_max_last;
+  if (n_selected_last) *n_selected_last = md->n_selected_last;
+  if (pressure_last_bar) *pressure_last_bar = md->pressure_last;
+  if (cell)
+    for (int k = 0; k < 9; ++k) cell[k] = md->cell[k];
   return MTP_OK;
 }
 
@@ -500,6 +677,9 @@ void mtp_md_free(mtp_md* md) {
   md->tmp.release();
   md->e_atom.release();
   md->small.release();
+  md->gamma.release();
+  md->flags.release();
+  md->sel_count.release();
   delete md;
 }
 

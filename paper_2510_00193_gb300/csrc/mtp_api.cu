@@ -64,16 +64,20 @@ __global__ void fixed_point_kernel(const double* __restrict__ x, const int32_t* 
   const double s2 = px * h2 + py * h5 + pz * h8;
   const double k = 4294967296.0;
   const double lim = 2147483647.0;
+  const int zi = z[i];
+  const bool z_ok = zi >= 0 && zi < S;
+  if (!z_ok) atomicCAS(status, 0, MTP_ERR_ARG);
+  out[4 * i + 3] = z_ok ? (long long)zi : 0ll;   // out-of-range species read as 0 (reported above)
   if (!(fabs(s0) < lim && fabs(s1) < lim && fabs(s2) < lim)) {
+    // non-finite (or absurdly far) position: reported, stored as the origin so
+    // that no kernel reads undefined coordinates
     atomicCAS(status, 0, MTP_ERR_NONFINITE);
+    out[4 * i] = out[4 * i + 1] = out[4 * i + 2] = 0ll;
     return;
   }
-  const int zi = z[i];
-  if (zi < 0 || zi >= S) atomicCAS(status, 0, MTP_ERR_ARG);
   out[4 * i] = __double2ll_rn(s0 * k);
   out[4 * i + 1] = __double2ll_rn(s1 * k);
   out[4 * i + 2] = __double2ll_rn(s2 * k);
-  out[4 * i + 3] = (long long)zi;
 }
 
 // Mixed path: the FP32 force accumulator converted to the FP64 output.
@@ -221,6 +225,49 @@ int mtp_load_params(const mtp_params_desc* d, mtp_handle** out) {
   return MTP_OK;
 }
 
+}  // extern "C"
+
+namespace mtp {
+// theta = [ s (S) | c (n_rad, [mu][k][zi][zj]) | xi (m) ] -> the handle's FP64
+// and FP32 parameter copies; a non-finite entry sets the status word.
+__global__ void set_theta_kernel(const double* __restrict__ theta, int S, int64_t nrad, int m,
+                                 double* __restrict__ species, double* __restrict__ radial_d,
+                                 double* __restrict__ xi_d, float* __restrict__ radial_f, float* __restrict__ xi_f,
+                                 int* __restrict__ status) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t n = S + nrad + m;
+  if (t >= n) return;
+  const double v = theta[t];
+  if (!isfinite(v)) atomicCAS(status, 0, MTP_ERR_NONFINITE);
+  if (t < S) {
+    species[t] = v;
+  } else if (t < S + nrad) {
+    radial_d[t - S] = v;
+    radial_f[t - S] = (float)v;
+  } else {
+    xi_d[t - S - nrad] = v;
+    xi_f[t - S - nrad] = (float)v;
+  }
+}
+}  // namespace mtp
+
+extern "C" {
+
+int mtp_set_theta(mtp_handle* h, const double* theta_dev, void* stream) {
+  using namespace mtp;
+  if (!h || !theta_dev) {
+    set_error("mtp_set_theta: invalid argument");
+    return MTP_ERR_ARG;
+  }
+  const int S = h->n_species;
+  const int64_t nrad = (int64_t)h->n_mu * h->n_q * S * S;
+  set_theta_kernel<<<(unsigned)((h->n_params + 255) / 256), 256, 0, (cudaStream_t)stream>>>(
+      theta_dev, S, nrad, h->m, h->species.as<double>(), h->radial_d.as<double>(), h->xi_d.as<double>(),
+      h->radial_f.as<float>(), h->xi_f.as<float>(), h->status.as<int>());
+  MTP_TRY_CUDA(cudaGetLastError());
+  return MTP_OK;
+}
+
 void mtp_free(mtp_handle* h) {
   if (!h) return;
   h->species.release();
@@ -353,6 +400,15 @@ int mtp_compute_efv(mtp_handle* h, const mtp_nlist* nl, const double* x, const i
   if (chunk_atoms < 0) {
     set_error("mtp_compute_efv: chunk_atoms < 0");
     return MTP_ERR_ARG;
+  }
+  {
+    const double det = cell[0] * (cell[4] * cell[8] - cell[5] * cell[7]) -
+                       cell[1] * (cell[3] * cell[8] - cell[5] * cell[6]) +
+                       cell[2] * (cell[3] * cell[7] - cell[4] * cell[6]);
+    if (!(std::fabs(det) > 0.0) || !std::isfinite(det)) {
+      set_error("mtp_compute_efv: singular or non-finite cell (det = %g)", det);
+      return MTP_ERR_ARG;
+    }
   }
   cudaStream_t s = (cudaStream_t)stream;
   if (precision == MTP_FP64 || n == 0) MTP_TRY_CUDA(cudaMemsetAsync(forces, 0, sizeof(double) * 3 * (size_t)n, s));

@@ -45,6 +45,14 @@ __host__ __device__ inline void unpack_image(int32_t p, int& n1, int& n2, int& n
   n3 = (int)((u >> 20) & 1023u) - kImageBias;
 }
 
+// Species index of atom i as the kernels use it: a value outside 0..S-1
+// (reported through the status word by the entry point's checks) is read as
+// species 0, so that no table lookup leaves its array.
+__device__ __forceinline__ int species_at(const int32_t* z, int64_t i, int S) {
+  const int v = __ldg(z + i);
+  return (unsigned)v < (unsigned)S ? v : 0;
+}
+
 // Everything an energy/force launch needs, passed by value.
 struct EfvArgs {
   int64_t atom_begin, atom_end, n_atoms;

@@ -285,6 +285,13 @@ int build_neighbors(mtp_nlist* nl, const double* x, int64_t n, const double* cel
   unsigned long long ext_bits[6];
   MTP_TRY_CUDA(cudaMemcpyAsync(ext_bits, extent, sizeof(ext_bits), cudaMemcpyDeviceToHost, stream));
   MTP_TRY_CUDA(cudaStreamSynchronize(stream));
+  if (n > 0)
+    for (int k = 0; k < 6; ++k)
+      if (!std::isfinite(unordered_bits(ext_bits[k]))) {
+        // a NaN or infinite position reaches the extent of its fractional coordinate
+        set_error("mtp_build_neighbors: non-finite position");
+        return MTP_ERR_NONFINITE;
+      }
   int64_t nbins = 1;
   for (int k = 0; k < 3; ++k) {
     if (g.pbc[k]) {

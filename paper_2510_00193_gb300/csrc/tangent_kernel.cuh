@@ -64,7 +64,7 @@ __global__ void __launch_bounds__(kEfvThreads) tangent_kernel(const TangentArgs 
   if (i < a.atom_end) {
     TangentGeom<S> geom;
     geom.load_centre(t, i, cell_of<S>(a));
-    const int zi = __ldg(a.z + i);
+    const int zi = species_at(a.z, i, a.n_species);
     const int64_t beg = __ldg(a.offsets + i), end = __ldg(a.offsets + i + 1);
     R M[LV::NCOMP];
 #pragma unroll
@@ -181,7 +181,7 @@ __global__ void __launch_bounds__(kEfvThreads) tangent_moments_kernel(const Tang
   const int64_t i = a.atom_begin + u;
   TangentGeom<S> geom;
   geom.load_centre(t, i, cell_of<S>(a));
-  const int zi = __ldg(a.z + i);
+  const int zi = species_at(a.z, i, a.n_species);
   const int64_t beg = __ldg(a.offsets + i), end = __ldg(a.offsets + i + 1);
   const R rcut = R(sm.rcut), mid = R(sm.mid), scale = R(sm.scale);
   R* buf = static_cast<R*>(a.mbuf) + u;
@@ -258,7 +258,7 @@ __global__ void __launch_bounds__(kEfvThreads) tangent_adjoint_kernel(const Tang
     const int64_t i = a.atom_begin + u;
     TangentGeom<S> geom;
     geom.load_centre(t, i, cell_of<S>(a));
-    const int zi = __ldg(a.z + i);
+    const int zi = species_at(a.z, i, a.n_species);
     const int64_t beg = __ldg(a.offsets + i), end = __ldg(a.offsets + i + 1);
     const R rcut = R(sm.rcut), mid = R(sm.mid), scale = R(sm.scale);
     const R* buf = static_cast<const R*>(a.mbuf) + (size_t)LV::NCOMP * n + u;

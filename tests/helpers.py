@@ -61,3 +61,41 @@ def oracle_sampled(model, st, r_cut, centres, force_atoms=()):
         forces.append(out["f"][k])
     res["forces"] = np.array(forces)
     return res
+
+
+class BinnedCandidates:
+    """Candidate atoms near a centre from a grid of fractional bins at least
+    ``radius`` high (valid when every cell height exceeds three bins): the
+    atoms of the 27 bins around the centre's bin, periodic in every axis."""
+
+    def __init__(self, st, radius):
+        inv = np.linalg.inv(st.cell)
+        h = 1.0 / np.linalg.norm(inv, axis=0)
+        self.nb = np.maximum(1, np.floor(h / radius).astype(int))
+        assert np.all(self.nb >= 3)
+        frac = (st.x @ inv) % 1.0
+        self.bin = np.minimum((frac * self.nb).astype(int), self.nb - 1)
+        key = (self.bin[:, 0] * self.nb[1] + self.bin[:, 1]) * self.nb[2] + self.bin[:, 2]
+        self.order = np.argsort(key, kind="stable")
+        self.start = np.searchsorted(key[self.order], np.arange(int(np.prod(self.nb)) + 1))
+
+    def __call__(self, c):
+        b = self.bin[c]
+        out = []
+        for d0 in (-1, 0, 1):
+            for d1 in (-1, 0, 1):
+                for d2 in (-1, 0, 1):
+                    q = (b + (d0, d1, d2)) % self.nb
+                    k = (q[0] * self.nb[1] + q[1]) * self.nb[2] + q[2]
+                    out.append(self.order[self.start[k]:self.start[k + 1]])
+        return np.unique(np.concatenate(out))
+
+
+def oracle_rows(st, r_cut, centre, cand):
+    """The oracle's neighbour rows (j, n) of one centre, computed on the
+    sub-array of its candidates (the same coordinates, so the same arithmetic)
+    and mapped back to the full structure's atom indices."""
+    sub = np.union1d(cand, [centre])
+    loc = int(np.searchsorted(sub, centre))
+    _, j, n = O.neighbor_list(st.x[sub], st.cell, st.pbc, r_cut, query=[loc])
+    return sub[j], n

@@ -38,7 +38,7 @@ def gpu_loss_grad(P, name, st, ft, precision):
     x = torch.tensor(st.x, dtype=torch.float64, device="cuda", requires_grad=True)
     z = torch.tensor(st.z, device="cuda")
     nl = P.mtp_build_neighbors(pot, x.detach(), st.cell, st.pbc)
-    theta = torch.zeros(pot.n_params, dtype=torch.float64, device="cuda", requires_grad=True)
+    theta = pot.initial_theta().requires_grad_(True)
     e = energy(pot, nl, x, z, st.cell, theta, precision)
     (gx,) = torch.autograd.grad(e, x, create_graph=True)
     f = -gx
@@ -110,3 +110,38 @@ def test_full_size_config3_directional_derivatives(P):
     fd_f = (-vals[2][1] + 8 * vals[1][1] - 8 * vals[-1][1] + vals[-2][1]) / (12 * h)
     assert np.abs(tan["dtheta_tan"].cpu().numpy() - fd_t).max() <= 1e-5 * np.abs(fd_t).max()
     assert np.abs(tan["force_tan"].cpu().numpy() - fd_f).max() <= 1e-5 * np.abs(fd_f).max()
+
+
+def test_theta_drives_the_potential(P):
+    """theta passed to the autograd energy is uploaded into the handle: with
+    every xi doubled and the species energies shifted, the energy, forces and
+    force-matching gradient equal those of a potential loaded with those
+    parameters, and the original theta gives the original energy back."""
+    from paper_2510_00193_gb300.autograd import energy
+    name = "bcc-l16-s3"
+    st = structure(*CASES[name])
+    d = pot_dict(name)
+    pot = P.Potential.from_dict(d)
+    d2 = dict(d)
+    d2["xi"] = [2.0 * v for v in d["xi"]]
+    d2["species_energy"] = [v + 0.25 for v in d["species_energy"]]
+    pot2 = P.Potential.from_dict(d2)
+    z = torch.tensor(st.z, device="cuda")
+    x = torch.tensor(st.x, dtype=torch.float64, device="cuda", requires_grad=True)
+    nl = P.mtp_build_neighbors(pot, x.detach(), st.cell, st.pbc)
+    theta2 = pot2.initial_theta().requires_grad_(True)
+    e = energy(pot, nl, x, z, st.cell, theta2, P.MTP_FP64)
+    (gx,) = torch.autograd.grad(e, x, create_graph=True)
+    ft = torch.tensor(synth.target_forces(st.n, 9), device="cuda")
+    loss = ((-gx - ft) ** 2).sum() / (3 * st.n)
+    loss.backward()
+    ref = P.mtp_compute_efv(pot2, nl, x.detach(), z, st.cell, precision=P.MTP_FP64, dtheta=True)
+    assert abs(e.item() - ref["e_total"].item()) <= 1e-12 * abs(ref["e_total"].item())
+    assert torch.allclose(-gx.detach(), ref["forces"], rtol=0, atol=1e-10)
+    tan = P.mtp_compute_efv_tangent(pot2, nl, x.detach(), z, st.cell, (ref["forces"] - ft).contiguous(),
+                                    precision=P.MTP_FP64)
+    want = -2.0 / (3 * st.n) * tan["dtheta_tan"]
+    assert torch.allclose(theta2.grad, want, rtol=0, atol=1e-10 * want.abs().max().item())
+    e0 = energy(pot, nl, x.detach(), z, st.cell, pot.initial_theta(), P.MTP_FP64)
+    ref0 = P.mtp_compute_efv(P.Potential.from_dict(d), nl, x.detach(), z, st.cell, precision=P.MTP_FP64)
+    assert abs(e0.item() - ref0["e_total"].item()) <= 1e-12 * abs(ref0["e_total"].item())

@@ -215,3 +215,113 @@ def test_md_full_size_list_and_sampled_forces(P):
     ref = oracle_sampled(oracle_model("bcc-l16-s3"), fin, pot.r_cut, atoms, force_atoms=atoms)
     got = f.cpu().numpy()[atoms]
     assert np.sqrt(((got - ref["forces"]) ** 2).mean()) <= 1e-4
+
+
+def test_md_npt_fp64_matches_oracle(P):
+    """Berendsen NPT (isotropic, strong coupling so that the cell moves by
+    ~1e-4 per step) against the oracle's berendsen_npt: positions, velocities,
+    cell and pressure after 6 steps of 1 fs (FP64 forces)."""
+    name = "bcc-l8-s1"
+    st = synth.crystal("bcc", (4, 4, 4), 3.16, 0.05, 1, 1)
+    pot = P.Potential.from_dict(pot_dict(name))
+    masses = [183.84]
+    v0 = start(st, masses, 300.0, 13)
+    dt, n_steps, p0, tau, bulk = 1e-3, 6, 0.0, 1e-2, 1e7
+    x = torch.tensor(st.x, device="cuda")
+    z = torch.tensor(st.z, dtype=torch.int32, device="cuda")
+    v = torch.tensor(v0, device="cuda")
+    md = P.MD(pot, x, st.cell, st.pbc, skin=0.3)
+    md.set_barostat(p0, tau, bulk)
+    f = P.mtp_compute_efv(pot, md.nlist(), x, z, st.cell, precision=P.MTP_FP64)["forces"]
+    assert md.run(x, v, z, masses, dt, n_steps, f, rebuild_every=-1, precision=P.MTP_FP64) == 0
+    info = md.info()
+    xo, vo, fo, cello, pro = O.berendsen_npt(oracle_model(name), st.x, v0, st.z, st.cell, st.pbc, masses, dt,
+                                             n_steps, p0, tau, bulk)
+    assert abs(np.linalg.det(cello) / np.linalg.det(st.cell) - 1) > 1e-5   # the cell moved
+    assert np.abs(info["cell"] - cello).max() <= 1e-12 * np.abs(cello).max()
+    assert info["pressure_bar"] == pytest.approx(pro[-1], rel=1e-8, abs=1e-6)
+    assert np.abs(x.cpu().numpy() - xo).max() <= 1e-9
+    assert np.abs(v.cpu().numpy() - vo).max() <= 1e-7
+    assert np.abs(f.cpu().numpy() - fo).max() <= 1e-8
+    # the exact list at the final (scaled) positions equals a fresh build in the final cell
+    mine = list_arrays(md.nlist())
+    fresh = list_arrays(P.mtp_build_neighbors(pot, x, info["cell"], st.pbc))
+    for a, b in zip(mine, fresh):
+        assert np.array_equal(a, b)
+
+
+def _active(P):
+    import json
+    import os
+    with open(os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "potentials",
+                           "bcc-l16-s1-active.json")) as fh:
+        act = json.load(fh)
+    m = act["m"]
+    return np.asarray(act["a_inv"]).reshape(m, m)
+
+
+def test_md_grade_every_x_steps_matches_oracle(P):
+    """The grade evaluated inside the run every 2 steps (paper: every X steps
+    of the MD): the largest grade of the last evaluation and the selection
+    flags accumulated over the run equal the oracle's grades of the oracle
+    trajectory at steps 2, 4 and 6 (FP64 forces, level 16, 128 atoms)."""
+    name = "bcc-l16-s1"
+    st = synth.crystal("bcc", (4, 4, 4), 3.16, 0.12, 1, 5)
+    pot = P.Potential.from_dict(pot_dict(name))
+    masses = [183.84]
+    v0 = start(st, masses, 300.0, 14)
+    a_inv = _active(P)
+    dt, every, n_steps = 1e-3, 2, 6
+    x = torch.tensor(st.x, device="cuda")
+    z = torch.tensor(st.z, dtype=torch.int32, device="cuda")
+    v = torch.tensor(v0, device="cuda")
+    md = P.MD(pot, x, st.cell, st.pbc, skin=0.3)
+    model = oracle_model(name)
+    # oracle trajectory and grades at the evaluation steps
+    xo, vo, fo = st.x, v0, None
+    gam = []
+    for _ in range(n_steps // every):
+        xo, vo, fo, _, _ = O.velocity_verlet(model, xo, vo, st.z, st.cell, st.pbc, masses, dt, every, f=fo)
+        b = O.basis_matrix(model, xo, st.z, st.cell, O.neighbor_list(xo, st.cell, st.pbc, pot.r_cut))
+        gam.append(O.grade(b, a_inv))
+    gam = np.array(gam)
+    tau_sel = float(np.median(gam))          # about half the atoms selected at some step
+    tau_brk = float(gam.max()) * 10.0
+    flags_ref = np.zeros(st.n, dtype=np.uint8)
+    for g in gam:
+        flags_ref |= O.grade_flags(g, tau_sel, tau_brk).astype(np.uint8)
+    sel = torch.zeros(st.n, dtype=torch.uint8, device="cuda")
+    a_inv_d = torch.tensor(a_inv, device="cuda")
+    md.set_grade(a_inv_d, every, tau_sel, tau_brk, P.MTP_GRADE_TENSOR, sel)
+    f = P.mtp_compute_efv(pot, md.nlist(), x, z, st.cell, precision=P.MTP_FP64)["forces"]
+    assert md.run(x, v, z, masses, dt, n_steps, f, rebuild_every=-1, precision=P.MTP_FP64) == 0
+    info = md.info()
+    assert info["grade_evals"] == n_steps // every
+    assert info["gamma_max_last"] == pytest.approx(gam[-1].max(), rel=1e-7)
+    assert info["n_selected_last"] == int((gam[-1] > tau_sel).sum())
+    assert np.array_equal(sel.cpu().numpy(), flags_ref)
+    assert np.abs(x.cpu().numpy() - xo).max() <= 1e-9
+
+
+def test_md_grade_break_stops_the_run(P):
+    """A break threshold below the grades stops mtp_md_run with
+    MTP_STATUS_BREAK right after the first evaluation step; the completed
+    step's state is kept and the run can continue after the grade is off."""
+    name = "bcc-l16-s1"
+    st = synth.crystal("bcc", (4, 4, 4), 3.16, 0.12, 1, 5)
+    pot = P.Potential.from_dict(pot_dict(name))
+    masses = [183.84]
+    v0 = start(st, masses, 300.0, 14)
+    x = torch.tensor(st.x, device="cuda")
+    z = torch.tensor(st.z, dtype=torch.int32, device="cuda")
+    v = torch.tensor(v0, device="cuda")
+    md = P.MD(pot, x, st.cell, st.pbc, skin=0.3)
+    md.set_grade(torch.tensor(_active(P), device="cuda"), 3, 1e-3, 1e-3, P.MTP_GRADE_FP64)
+    f = P.mtp_compute_efv(pot, md.nlist(), x, z, st.cell, precision=P.MTP_MIXED)["forces"]
+    assert md.run(x, v, z, masses, 1e-3, 10, f, rebuild_every=-1, precision=P.MTP_MIXED) == P.MTP_STATUS_BREAK
+    info = md.info()
+    assert info["steps"] == 3 and info["grade_evals"] == 1
+    assert info["n_selected_last"] == st.n
+    md.set_grade(None, 0)
+    assert md.run(x, v, z, masses, 1e-3, 2, f, rebuild_every=-1, precision=P.MTP_MIXED) == 0
+    assert md.info()["steps"] == 5

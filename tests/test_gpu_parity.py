@@ -193,7 +193,9 @@ def test_level20_split_kernels_in_chunks_match_oracle(P):
     a = run_gpu(P, name, st, P.MTP_MIXED, dtheta=True)
     b = run_gpu(P, name, st, P.MTP_MIXED, dtheta=True, chunk=37)
     assert np.abs(a["e_atom"] - b["e_atom"]).max() <= 1e-9
-    assert np.abs(a["forces"] - b["forces"]).max() <= 1e-5
+    # FP32 force atomics add each atom's ~2 x 54 pair terms in an order that
+    # depends on the launch: a few units in the last place of the largest force
+    assert np.abs(a["forces"] - b["forces"]).max() <= 2.0 ** -17 * max(1.0, np.abs(a["forces"]).max())
 
 
 def test_empty_and_isolated_atoms(P):

@@ -649,3 +649,51 @@ def test_maxvol_ties_go_to_the_lowest_row():
 def test_grade_flags():
     gam = np.array([0.5, 2.0, 2.0000001, 9.99, 10.0, 10.5])
     assert O.grade_flags(gam, 2.0, 10.0).tolist() == [0, 0, 1, 1, 1, 3]
+
+
+def test_berendsen_with_infinite_tau_is_velocity_verlet():
+    """With tau_p so long that the scale factor rounds to 1, the NPT
+    integrator is the NVE one bit for bit and the cell does not move."""
+    model = O.load_model(pot_file("bcc-l8-s1"))
+    st, v0, masses = _md_start(43)
+    dt, n = 1e-3, 3
+    x1, v1, f1, _, _ = O.velocity_verlet(model, st.x, v0, st.z, st.cell, st.pbc, masses, dt, n)
+    x2, v2, f2, cell2, _ = O.berendsen_npt(model, st.x, v0, st.z, st.cell, st.pbc, masses, dt, n, 1.0, 1e300)
+    assert np.array_equal(x1, x2) and np.array_equal(v1, v2) and np.array_equal(f1, f2)
+    assert np.array_equal(cell2, st.cell)
+
+
+def test_pressure_virial_term_is_minus_dE_dV():
+    """For a static configuration the pressure is -dE/dV under isotropic
+    scaling of the cell and positions (central differences in the volume)."""
+    model = O.load_model(pot_file("bcc-l8-s1"))
+    st = synth.crystal("bcc", (3, 3, 3), 3.16, 0.08, 1, 44)
+    r_cut = model.pot.r_cut
+    out = O.evaluate(model, st.x, st.z, st.cell, O.neighbor_list(st.x, st.cell, st.pbc, r_cut), want=("e", "w"))
+    p = O.pressure_bar(0.0, out["w"], st.cell) / O.EV_PER_A3_IN_BAR
+    h = 1e-5
+    ev = []
+    for s in (1 + h, 1 - h):
+        x, c = st.x * s, st.cell * s
+        e = O.evaluate(model, x, st.z, c, O.neighbor_list(x, c, st.pbc, r_cut), want=("e",))["e"]
+        ev.append((e, abs(np.linalg.det(c))))
+    p_fd = -(ev[0][0] - ev[1][0]) / (ev[0][1] - ev[1][1])
+    assert p == pytest.approx(p_fd, rel=1e-6, abs=1e-9)
+
+
+def test_berendsen_ideal_gas_relaxes_to_the_ideal_gas_volume():
+    """With every xi = 0 (no forces, zero virial) the atoms fly freely and the
+    pressure is the kinetic 2 E_kin / (3 V); the barostat drives the volume to
+    V* = 2 E_kin / (3 p_target), the ideal-gas law written in SI units."""
+    model = O.load_model(pot_file("bcc-l8-s1"))
+    model.xi = torch.zeros_like(model.xi)
+    st, v0, masses = _md_start(45, temperature=600.0)
+    p_target = 2000.0   # bar
+    dt, tau = 1e-3, 1e-2
+    x, v, f, cell, pr = O.berendsen_npt(model, st.x, v0, st.z, st.cell, st.pbc, masses, dt, 150, p_target, tau,
+                                        bulk_modulus=p_target)
+    ke_j = 0.5 * masses[0] * 1.66053906660e-27 * ((v0 * 1e2) ** 2).sum()   # A/ps = 100 m/s
+    v_star = 2.0 * ke_j / (3.0 * p_target * 1e5) * 1e30                    # A^3
+    assert np.array_equal(v, v0)
+    assert abs(np.linalg.det(cell)) == pytest.approx(v_star, rel=1e-6)
+    assert pr[-1] == pytest.approx(p_target, rel=1e-6)

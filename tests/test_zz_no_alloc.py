@@ -58,6 +58,80 @@ def test_noalloc_matches_regular_entry_point_on_two_calls(P):
         assert abs(g["e_total"][0] - r["e_total"][0]) <= 1e-5 * st.n
 
 
+def _compare(P, ref, got, n):
+    r = {k: v.cpu().numpy() for k, v in ref.items() if v is not None}
+    g = {k: v.cpu().numpy() for k, v in got.items()}
+    assert np.abs(g["e_atom"] - r["e_atom"]).max() <= 1e-5
+    assert np.abs(g["forces"] - r["forces"]).max() <= 1e-4
+    assert np.abs(g["virial"] - r["virial"]).max() <= 1e-4 * max(1.0, np.abs(r["virial"]).max())
+    assert abs(g["e_total"][0] - r["e_total"][0]) <= 1e-5 * n
+
+
+def test_noalloc_call_leaves_device_memory_unchanged(P):
+    """On a fresh handle, after one warm-up call (which looks up the scratch
+    array's address and loads the kernels), a call on the largest allowed
+    configuration (65,536 atoms, in chunks of 20,000 atoms) leaves the free
+    device memory unchanged: a regular call would first grow the handle's
+    buffers to that size."""
+    pot = P.Potential.from_dict(pot_dict("bcc-l16-s3"))
+    small = structure("bcc", (4, 4, 3), 3.16, 0.08, 3, 2, 1)
+    big = structure("bcc", (32, 32, 32), 3.16, 0.08, 3, 2, 2)
+    bufs = []
+    for st in (small, big):
+        x = torch.tensor(st.x, dtype=torch.float64, device="cuda")
+        z = torch.tensor(st.z, dtype=torch.int32, device="cuda")
+        nl = P.mtp_build_neighbors(pot, x, st.cell, st.pbc)
+        bufs.append((st, x, z, nl, _alloc(st.n)))
+    st, x, z, nl, out = bufs[0]
+    P.mtp_compute_efv_noalloc(pot, nl, x, z, st.cell, out, chunk_atoms=20000)
+    torch.cuda.synchronize()
+    st, x, z, nl, out = bufs[1]
+    free0, _ = torch.cuda.mem_get_info()
+    P.mtp_compute_efv_noalloc(pot, nl, x, z, st.cell, out, chunk_atoms=20000)
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info()
+    assert free1 == free0
+    assert P.mtp_device_status(pot) == 0
+    ref = P.mtp_compute_efv(pot, nl, x, z, st.cell, precision=P.MTP_MIXED)
+    torch.cuda.synchronize()
+    _compare(P, ref, out, st.n)
+
+
+def test_noalloc_level20_fused_path(P):
+    """Level 20 (the interpreted contraction) on a 32-atom FCC box, 4 species:
+    the fused kernel of this entry point against mtp_compute_efv's three-kernel
+    split, on two calls in a row.  The two are different FP32 evaluations, so
+    they agree within twice the mixed-precision bound of the other tests
+    (site energies 1e-5 eV + 64 u a_i, forces 1e-4 eV/A + 64 u A_k, with a_i
+    the sum of |xi_alpha B_alpha(i)| and A_k the sum of a over k and its
+    neighbours)."""
+    d = pot_dict("fcc-l20-s4")
+    pot = P.Potential.from_dict(d)
+    st = structure("fcc", (2, 2, 2), 3.6, 0.1, 4, 3)
+    x = torch.tensor(st.x, dtype=torch.float64, device="cuda")
+    z = torch.tensor(st.z, dtype=torch.int32, device="cuda")
+    nl = P.mtp_build_neighbors(pot, x, st.cell, st.pbc)
+    ref = P.mtp_compute_efv(pot, nl, x, z, st.cell, precision=P.MTP_MIXED)
+    rows = P.mtp_compute_basis_rows(pot, nl, x, z, st.cell)
+    a = (rows.abs() * torch.tensor(d["xi"], device="cuda").abs()).sum(1)
+    off, j, _ = nl.to_tensors()
+    ii = torch.repeat_interleave(torch.arange(st.n, device="cuda"), off[1:] - off[:-1])
+    A = a.clone().index_add_(0, ii, a[j.long()])
+    u = 2.0 ** -24
+    tol_e = (2 * (1e-5 + 64 * u * a)).cpu().numpy()
+    tol_f = (2 * (1e-4 + 64 * u * A)).cpu().numpy()
+    for _ in range(2):
+        got = P.mtp_compute_efv_noalloc(pot, nl, x, z, st.cell, _alloc(st.n))
+        torch.cuda.synchronize()
+        assert P.mtp_device_status(pot) == 0
+        r = {k: v.cpu().numpy() for k, v in ref.items() if v is not None}
+        g = {k: v.cpu().numpy() for k, v in got.items()}
+        assert np.all(np.abs(g["e_atom"] - r["e_atom"]) <= tol_e)
+        assert np.all(np.abs(g["forces"] - r["forces"]).max(axis=1) <= tol_f)
+        assert abs(g["e_total"][0] - r["e_total"][0]) <= tol_e.sum()
+        assert np.abs(g["virial"] - r["virial"]).max() <= 1e-4 * max(1.0, np.abs(r["virial"]).max())
+
+
 def test_noalloc_rejects_configurations_beyond_its_scratch(P):
     from paper_2510_00193_gb300 import _lib
     pot = P.Potential.from_dict(pot_dict("bcc-l16-s3"))
