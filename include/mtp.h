@@ -144,6 +144,25 @@ int mtp_compute_efv(mtp_handle* h, const mtp_nlist* nl, const double* x_dev, con
                     double* e_atom_dev, double* forces_dev, double* virial_dev, double* e_total_dev,
                     double* dEdtheta_dev, void* stream);
 
+/* Kernel for mtp_compute_efv (same results within rounding):
+ *   1: one thread per centre atom (the thread-parallel variant, for large
+ *      systems; paper Sec. 2.1, Table 1);
+ *   2: one warp per centre atom, the warp's lanes sharing the atom's pairs
+ *      (the block-parallel variant for small systems and high levels, paper
+ *      Sec. 2.1, Table 1, Sec. 4); levels up to 16 (levels 18 and 20 run one
+ *      thread per atom: MTP_ERR_UNSUPPORTED);
+ *   0 (default): the variant mtp_efv_tune measured faster for the atom count's
+ *      power-of-two size class, else warp per atom up to 8192 atoms. */
+int mtp_set_efv_variant(mtp_handle* h, int32_t variant);
+/* Times both variants on this configuration (one warm-up and three timed
+ * evaluations each, CUDA events on `stream`) and records the faster for its
+ * precision and power-of-two size class in the handle.  chosen (HOST,
+ * nullable): 1 or 2; ms (HOST [2], nullable): mean ms per evaluation of each
+ * (0 for a variant the level does not have).  Allocates scratch outputs for
+ * the call; synchronises `stream`. */
+int mtp_efv_tune(mtp_handle* h, const mtp_nlist* nl, const double* x_dev, const int32_t* z_dev, int64_t n_atoms,
+                 const double* cell, int32_t precision, int32_t* chosen, float* ms, void* stream);
+
 /* Directional second derivatives, for the parameter gradient of a loss on
  * forces (double backward): with v_dev (DEVICE [N][3]) a direction of the
  * positions, dtheta_tan_dev [n_params] = d/dt dE/dtheta (x + t v) and
@@ -187,6 +206,30 @@ int mtp_compute_grade(mtp_handle* h, const mtp_nlist* nl, const double* x_dev, c
                       double tau_sel, double tau_brk, int64_t chunk_atoms, int32_t method, double* gamma_dev,
                       uint8_t* flags_dev, double* gamma_max, double* gamma_cfg, int64_t* n_ambiguous,
                       int64_t* n_rechecked, void* stream);
+
+/* Grade of caller-given rows against an active set: gamma_r = max_k
+ * |(b_r A^-1)_k|, with b_r = (rows_dev[r ld + c_0], ..., rows_dev[r ld +
+ * c_{m-1}]), c_j = cols_dev[j] (DEVICE int32 [m]) or j when cols_dev is NULL
+ * (then ld >= m); rows_dev DEVICE FP64 with row stride ld; a_inv_dev (DEVICE
+ * [m][m] FP64) the inverse of the active set; flags_dev bit 0 = gamma_r >
+ * tau_sel, bit 1 = gamma_r > tau_brk; all in FP64 (the kernel of
+ * MTP_GRADE_FP64).  This is the configuration mode of the grade over the full
+ * parameter gradient (paper Sec. 2.1; MLIP's configuration mode): b_r =
+ * dE/dtheta of configuration r (from mtp_compute_efv or mtp_compute_batch,
+ * ld = n_params) restricted to a set of linearly independent columns.  The
+ * full gradient always has at least n_mu (n_mu + 1) / 2 exact linear
+ * relations (E is
+ * unchanged to first order when f_mu gains a multiple of f_nu, nu <= mu, and
+ * xi compensates), so an active set over every column is singular; the
+ * columns are chosen once, on the pool the active set is drawn from.
+ * Outputs gamma_dev [n_rows], flags_dev [n_rows] (DEVICE); gamma_max and
+ * n_ambiguous (HOST, nullable; the count of grades within 1e-12 sum_j |b_rj|
+ * max_k |A^-1_jk| of a threshold).  m <= 16384.  Allocates 8 (m + 2) bytes of
+ * scratch for the call; synchronises `stream`.  Returns MTP_STATUS_BREAK when
+ * the largest grade exceeds tau_brk. */
+int mtp_grade_rows(const double* rows_dev, int64_t n_rows, int64_t ld, const int32_t* cols_dev, int32_t m,
+                   const double* a_inv_dev, double tau_sel, double tau_brk, double* gamma_dev, uint8_t* flags_dev,
+                   double* gamma_max, int64_t* n_ambiguous, void* stream);
 
 /* Verification hook for the tensor-core grade product (same kernel as
  * MTP_GRADE_TENSOR; the paper has no counterpart, it exists so that tests can

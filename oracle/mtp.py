@@ -652,6 +652,29 @@ def initial_rows(pool: np.ndarray) -> np.ndarray:
     return np.array(chosen)
 
 
+def independent_columns(pool: np.ndarray, rel_tol: float = 1e-9) -> np.ndarray:
+    """A maximal set of linearly independent columns of the pool (greedy
+    column-pivoted Gram-Schmidt on the columns scaled to unit norm, two
+    projection passes per step; stop when no residual exceeds rel_tol).
+    Returns the chosen column indices, sorted."""
+    p = np.array(pool, dtype=np.float64)
+    norms = np.linalg.norm(p, axis=0)
+    res = p / np.where(norms > 0, norms, 1.0)
+    basis, chosen = [], []
+    for _ in range(min(p.shape)):
+        r = np.linalg.norm(res, axis=0)
+        r[chosen] = -1.0
+        k = int(np.argmax(r))
+        if r[k] <= rel_tol:
+            break
+        chosen.append(k)
+        q = res[:, k] / r[k]
+        for _ in range(2):
+            res -= np.outer(q, q @ res)
+        basis.append(q)
+    return np.array(sorted(chosen), dtype=np.int64)
+
+
 def maxvol(pool: np.ndarray, rows=None, delta: float = 0.01, max_iter: int = 10000):
     """MaxVol: swap a pool row into the active set while some |(P A^-1)_ik|
     exceeds 1 + delta; ties go to the lowest i, then the lowest k.

@@ -238,6 +238,28 @@ def mtp_compute_efv(potential: Potential, nlist: NeighborList, x, z, cell, preci
     return out
 
 
+EFV_AUTO, EFV_THREAD_PER_ATOM, EFV_WARP_PER_ATOM = 0, 1, 2
+
+
+def mtp_set_efv_variant(potential: Potential, variant: int) -> None:
+    """Energy/force kernel: 0 tuned/auto, 1 one thread per atom, 2 one warp per atom."""
+    check(_lib.load().mtp_set_efv_variant(potential.handle, int(variant)))
+
+
+def mtp_efv_tune(potential: Potential, nlist: NeighborList, x, z, cell, precision=MTP_MIXED, stream=None) -> dict:
+    """Times both energy/force kernels on this configuration and records the
+    faster for its size class; returns {"chosen": 1 or 2, "ms": [thread, warp]}."""
+    import torch
+    n = x.shape[0]
+    c = _host_d(cell, 9)
+    ch = ctypes.c_int32()
+    ms = (ctypes.c_float * 2)()
+    check(_lib.load().mtp_efv_tune(potential.handle, nlist.handle, _dptr(x, torch.float64, 3 * n, "x"),
+                                   _dptr(z, torch.int32, n, "z"), n, c.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                   int(precision), ctypes.byref(ch), ms, _stream_ptr(stream)))
+    return {"chosen": ch.value, "ms": [ms[0], ms[1]]}
+
+
 def mtp_compute_efv_noalloc(potential: Potential, nlist: NeighborList, x, z, cell, out, chunk_atoms=0,
                             stream=None) -> dict:
     """Mixed-precision site energies, forces, virial and total energy into the
@@ -287,6 +309,28 @@ def mtp_compute_grade(potential: Potential, nlist: NeighborList, x, z, cell, a_i
         ctypes.byref(gmax), ctypes.byref(gcfg), ctypes.byref(amb), ctypes.byref(rchk), _stream_ptr(stream)))
     out.update(gamma_max=gmax.value, gamma_cfg=gcfg.value, n_ambiguous=amb.value, n_rechecked=rchk.value, status=rc)
     return out
+
+
+def mtp_grade_rows(rows, a_inv, tau_sel=2.0, tau_brk=10.0, cols=None, stream=None) -> dict:
+    """FP64 grade of the rows of ``rows`` [n, ld] (CUDA float64), restricted
+    to the columns ``cols`` (CUDA int32 [m], or all columns), against an
+    active-set inverse [m, m]: gamma [n], flags [n], gamma_max, n_ambiguous
+    and status (1 = above the break threshold).  With rows = dE/dtheta per
+    configuration this is the configuration-mode grade over the parameter
+    gradient."""
+    import torch
+    n, ld = rows.shape
+    m = int(cols.numel()) if cols is not None else ld
+    gamma = torch.empty(n, dtype=torch.float64, device=rows.device)
+    flags = torch.empty(n, dtype=torch.uint8, device=rows.device)
+    gmax, amb = ctypes.c_double(), ctypes.c_int64()
+    rc = check(_lib.load().mtp_grade_rows(
+        _dptr(rows, torch.float64, n * ld, "rows"), int(n), int(ld),
+        _dptr(cols, torch.int32, m, "cols") if cols is not None else None, int(m),
+        _dptr(a_inv, torch.float64, m * m, "a_inv"), float(tau_sel), float(tau_brk),
+        _dptr(gamma, torch.float64, n, "gamma"), _dptr(flags, torch.uint8, n, "flags"), ctypes.byref(gmax),
+        ctypes.byref(amb), _stream_ptr(stream)))
+    return {"gamma": gamma, "flags": flags, "gamma_max": gmax.value, "n_ambiguous": amb.value, "status": rc}
 
 
 def mtp_grade_tc_selftest(xs, ys, fexp, erow, n_rows, acc=None, stream=None):

@@ -90,6 +90,11 @@ SIGNATURES = {
     "mtp_last_error": (ctypes.c_char_p, []),
     "mtp_probe_fma": (ctypes.c_int, [_I32, _I64, _I32, _P_D, _P_D]),
     "mtp_set_wait_limit": (ctypes.c_int, [_I64]),
+    "mtp_set_efv_variant": (ctypes.c_int, [_VP, _I32]),
+    "mtp_efv_tune": (ctypes.c_int, [_VP, _VP, _VP, _VP, _I64, _P_D, _I32, _P_I32, ctypes.POINTER(ctypes.c_float),
+                                    _VP]),
+    "mtp_grade_rows": (ctypes.c_int, [_VP, _I64, _I64, _VP, _I32, _VP, ctypes.c_double, ctypes.c_double, _VP, _VP,
+                                      _P_D, _P_I64, _VP]),
 }
 
 _lib = None

@@ -63,7 +63,7 @@ def generate_sources(levels=LEVELS):
         _write(path, (
             "// Generated by paper_2510_00193_gb300/build.py.\n"
             "#include \"efv_kernel.cuh\"\n#include \"grade_kernel.cuh\"\n#include \"batch_kernel.cuh\"\n"
-            "#include \"tangent_kernel.cuh\"\n"
+            "#include \"tangent_kernel.cuh\"\n#include \"efv_team.cuh\"\n"
             "#include \"mtp_level%d.cuh\"\n"
             "namespace mtp {\nint efv_level%d(const EfvArgs& a, int precision, bool want_dtheta, cudaStream_t s) {\n"
             "  return efv_launch<MtpLevel%d>(a, precision, want_dtheta, s);\n}\n"
@@ -74,16 +74,19 @@ def generate_sources(levels=LEVELS):
             "int tangent_level%d(const TangentArgs& t, int precision, cudaStream_t s) {\n"
             "  return tangent_launch<MtpLevel%d>(t, precision, s);\n}\n"
             "int split_level%d() { return MtpLevel%d::NGROUPS > 1 ? MtpLevel%d::NCOMP : 0; }\n"
-            "}  // namespace mtp\n") % (L, L, L, L, L, L, L, L, L, L, L, L))
+            "int team_level%d(const EfvArgs& a, int precision, bool want_dtheta, cudaStream_t s) {\n"
+            "  return efv_team_launch<MtpLevel%d>(a, precision, want_dtheta, s);\n}\n"
+            "}  // namespace mtp\n") % (L, L, L, L, L, L, L, L, L, L, L, L, L, L))
         units.append(path)
     decl = "".join("int efv_level%d(const EfvArgs&, int, bool, cudaStream_t);\n"
                    "int rows_level%d(const EfvArgs&, const int32_t*, int64_t, double*, int64_t, double*, cudaStream_t);\n"
                    "int batch_level%d(const BatchArgs&, int, bool, int, cudaStream_t);\n"
                    "int tangent_level%d(const TangentArgs&, int, cudaStream_t);\n"
                    "int split_level%d();\n"
-                   % (L, L, L, L, L) for L in levels)
-    table = ",\n".join("  {%d, efv_level%d, rows_level%d, batch_level%d, tangent_level%d, split_level%d()}"
-                        % (L, L, L, L, L, L) for L in levels)
+                   "int team_level%d(const EfvArgs&, int, bool, cudaStream_t);\n"
+                   % (L, L, L, L, L, L) for L in levels)
+    table = ",\n".join("  {%d, efv_level%d, rows_level%d, batch_level%d, tangent_level%d, split_level%d(), team_level%d}"
+                        % (L, L, L, L, L, L, L) for L in levels)
     reg = os.path.join(GEN, "levels.cu")
     _write(reg, (
         "// Generated by paper_2510_00193_gb300/build.py.\n#include \"mtp_internal.cuh\"\nnamespace mtp {\n%s"

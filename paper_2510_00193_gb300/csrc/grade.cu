@@ -16,8 +16,9 @@
 // sum_j |b_ij| max_k |A_jk|; a row whose FP64 grade lies within eps_i of a
 // threshold is counted as ambiguous (its flag is still the FP64 comparison).
 //
-// gemm_grade_kernel: 64 rows x all m columns per block of 256 threads, K in
-// blocks of 16 staged in shared memory, 4 x 8 FP64 accumulators per thread,
+// gemm_grade_kernel: 64 rows x all m columns per block of 256 threads (in
+// column blocks of 128), K in blocks of 16 staged in shared memory, 4 x 8
+// FP64 accumulators per thread,
 // fused row maximum, bound, flags and the running maximum grade; rows come
 // either contiguously or from an index list.
 #include <cuda_runtime.h>
@@ -32,7 +33,11 @@ namespace mtp {
 constexpr double kGradeRelErr = 1e-12;
 constexpr int kGemmBM = 64, kGemmBK = 16, kGemmBN = 128;
 
-__global__ void __launch_bounds__(256) gemm_grade_kernel(const double* __restrict__ rows, int64_t n, int m,
+// Row r of the product is row `src` of `rows` (stride ld), entry j read at
+// column cols[j] when cols is given (else j): the configuration mode over the
+// parameter gradient grades a subset of its columns.
+__global__ void __launch_bounds__(256) gemm_grade_kernel(const double* __restrict__ rows, int64_t ld,
+                                                         const int32_t* __restrict__ cols, int64_t n, int m,
                                                          const double* __restrict__ ainv,
                                                          const double* __restrict__ amax, double tau_sel,
                                                          double tau_brk, double* __restrict__ gamma,
@@ -51,48 +56,51 @@ __global__ void __launch_bounds__(256) gemm_grade_kernel(const double* __restric
     n = (int64_t)*list_n;   // rows are list[0 .. *list_n)
     if (row0 >= n) return;  // uniform over the block
   }
-  double acc[4][8];
+  double rmax[4] = {0.0, 0.0, 0.0, 0.0};
+  for (int cb = 0; cb < m; cb += kGemmBN) {   // column blocks of A^-1 (one for m <= 128)
+    double acc[4][8];
 #pragma unroll
-  for (int r = 0; r < 4; ++r)
+    for (int r = 0; r < 4; ++r)
 #pragma unroll
-    for (int c = 0; c < 8; ++c) acc[r][c] = 0.0;
-  for (int kb = 0; kb < m; kb += kGemmBK) {
+      for (int c = 0; c < 8; ++c) acc[r][c] = 0.0;
+    for (int kb = 0; kb < m; kb += kGemmBK) {
 #pragma unroll
-    for (int t = 0; t < (kGemmBM * kGemmBK) / 256; ++t) {
-      const int e = tid + 256 * t;
-      const int rr = e / kGemmBK, kk = e % kGemmBK;
-      const int64_t gr = row0 + rr;
-      const int64_t src = (gr < n && list) ? (int64_t)list[gr] : gr;
-      As[kk][rr] = (gr < n && kb + kk < m) ? rows[src * m + kb + kk] : 0.0;
+      for (int t = 0; t < (kGemmBM * kGemmBK) / 256; ++t) {
+        const int e = tid + 256 * t;
+        const int rr = e / kGemmBK, kk = e % kGemmBK;
+        const int64_t gr = row0 + rr;
+        const int64_t src = (gr < n && list) ? (int64_t)list[gr] : gr;
+        const int col = kb + kk;
+        As[kk][rr] = (gr < n && col < m) ? rows[src * ld + (cols ? cols[col] : col)] : 0.0;
+      }
+#pragma unroll
+      for (int t = 0; t < (kGemmBK * kGemmBN) / 256; ++t) {
+        const int e = tid + 256 * t;
+        const int kk = e / kGemmBN, cc = e % kGemmBN;
+        Bs[kk][cc] = (kb + kk < m && cb + cc < m) ? ainv[(int64_t)(kb + kk) * m + cb + cc] : 0.0;
+      }
+      __syncthreads();
+#pragma unroll
+      for (int kk = 0; kk < kGemmBK; ++kk) {
+        double av[4], bv[8];
+#pragma unroll
+        for (int r = 0; r < 4; ++r) av[r] = As[kk][ty * 4 + r];
+#pragma unroll
+        for (int c = 0; c < 8; ++c) bv[c] = Bs[kk][tx + 16 * c];
+#pragma unroll
+        for (int r = 0; r < 4; ++r)
+#pragma unroll
+          for (int c = 0; c < 8; ++c) acc[r][c] = fma(av[r], bv[c], acc[r][c]);
+      }
+      __syncthreads();
     }
 #pragma unroll
-    for (int t = 0; t < (kGemmBK * kGemmBN) / 256; ++t) {
-      const int e = tid + 256 * t;
-      const int kk = e / kGemmBN, cc = e % kGemmBN;
-      Bs[kk][cc] = (kb + kk < m && cc < m) ? ainv[(int64_t)(kb + kk) * m + cc] : 0.0;
-    }
-    __syncthreads();
+    for (int r = 0; r < 4; ++r)
 #pragma unroll
-    for (int kk = 0; kk < kGemmBK; ++kk) {
-      double av[4], bv[8];
-#pragma unroll
-      for (int r = 0; r < 4; ++r) av[r] = As[kk][ty * 4 + r];
-#pragma unroll
-      for (int c = 0; c < 8; ++c) bv[c] = Bs[kk][tx + 16 * c];
-#pragma unroll
-      for (int r = 0; r < 4; ++r)
-#pragma unroll
-        for (int c = 0; c < 8; ++c) acc[r][c] = fma(av[r], bv[c], acc[r][c]);
-    }
-    __syncthreads();
+      for (int c = 0; c < 8; ++c) rmax[r] = fmax(rmax[r], fabs(acc[r][c]));
   }
 #pragma unroll
-  for (int r = 0; r < 4; ++r) {
-    double mx = 0.0;
-#pragma unroll
-    for (int c = 0; c < 8; ++c) mx = fmax(mx, fabs(acc[r][c]));
-    red[ty * 4 + r][tx] = mx;
-  }
+  for (int r = 0; r < 4; ++r) red[ty * 4 + r][tx] = rmax[r];
   __syncthreads();
   if (tid < kGemmBM) {
     int64_t gr = row0 + tid;
@@ -101,7 +109,7 @@ __global__ void __launch_bounds__(256) gemm_grade_kernel(const double* __restric
       double g = 0.0;
       for (int t = 0; t < 16; ++t) g = fmax(g, red[tid][t]);
       double bound = 0.0;
-      for (int j = 0; j < m; ++j) bound = fma(fabs(rows[gr * m + j]), amax[j], bound);
+      for (int j = 0; j < m; ++j) bound = fma(fabs(rows[gr * ld + (cols ? cols[j] : j)]), amax[j], bound);
       bound *= kGradeRelErr;
       gamma[gr] = g;
       flags[gr] = (uint8_t)((g > tau_sel ? 1 : 0) | (g > tau_brk ? 2 : 0));
@@ -298,13 +306,15 @@ extern "C" int mtp_compute_grade(mtp_handle* h, const mtp_nlist* nl, const doubl
                             s)) != MTP_OK)
         return rc;
       gemm_grade_kernel<<<(unsigned)((cnt + kGemmBM - 1) / kGemmBM), 256, 0, s>>>(
-          rows, cnt, m, a_inv, amax, tau_sel, tau_brk, gamma + b, flags + b, gmax_bits, n_amb, list, list_n);
+          rows, m, nullptr, cnt, m, a_inv, amax, tau_sel, tau_brk, gamma + b, flags + b, gmax_bits, n_amb, list,
+          list_n);
       MTP_TRY_CUDA(cudaGetLastError());
       add_count_kernel<<<1, 1, 0, s>>>(n_rchk, list_n);
       MTP_TRY_CUDA(cudaGetLastError());
     } else if (a_inv) {
       gemm_grade_kernel<<<(unsigned)((cnt + kGemmBM - 1) / kGemmBM), 256, 0, s>>>(
-          rows, cnt, m, a_inv, amax, tau_sel, tau_brk, gamma + b, flags + b, gmax_bits, n_amb, nullptr, nullptr);
+          rows, m, nullptr, cnt, m, a_inv, amax, tau_sel, tau_brk, gamma + b, flags + b, gmax_bits, n_amb, nullptr,
+          nullptr);
       MTP_TRY_CUDA(cudaGetLastError());
     }
   }
@@ -372,4 +382,55 @@ extern "C" int mtp_grade_tc_selftest(const uint16_t* xs, const uint16_t* ys, con
     return st;
   }
   return MTP_OK;
+}
+
+// Grade of caller-given rows (configuration mode over the full parameter
+// gradient, see mtp.h): the FP64 row-max product with its error bound.
+extern "C" int mtp_grade_rows(const double* rows, int64_t n_rows, int64_t ld, const int32_t* cols, int32_t m,
+                              const double* a_inv, double tau_sel, double tau_brk, double* gamma, uint8_t* flags,
+                              double* gamma_max, int64_t* n_ambiguous, void* stream) {
+  if (n_rows < 0 || m < 1 || (n_rows > 0 && (!rows || !a_inv || !gamma || !flags)) || (!cols && ld < m) || ld < 1) {
+    set_error("mtp_grade_rows: invalid argument");
+    return MTP_ERR_ARG;
+  }
+  if (!(tau_sel > 0.0) || !(tau_brk >= tau_sel)) {
+    set_error("mtp_grade_rows: thresholds must satisfy 0 < tau_sel <= tau_brk");
+    return MTP_ERR_ARG;
+  }
+  if (m > 16384) {
+    set_error("mtp_grade_rows: m = %d exceeds 16384", (int)m);
+    return MTP_ERR_ARG;
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  // scratch: gmax bits, ambiguous count, then max_k |A^-1_jk| [m]
+  void* scratch = nullptr;
+  MTP_TRY_CUDA(cudaMalloc(&scratch, sizeof(double) * (2 + (size_t)m)));
+  unsigned long long* gmax_bits = static_cast<unsigned long long*>(scratch);
+  unsigned long long* n_amb = gmax_bits + 1;
+  double* amax = reinterpret_cast<double*>(gmax_bits + 2);
+  unsigned long long host[2] = {0ull, 0ull};
+  cudaError_t e = cudaMemsetAsync(scratch, 0, sizeof(unsigned long long) * 2, s);
+  if (e == cudaSuccess) {
+    row_absmax_kernel<<<(unsigned)((m + 127) / 128), 128, 0, s>>>(a_inv, m, amax);
+    if (n_rows > 0)
+      gemm_grade_kernel<<<(unsigned)((n_rows + kGemmBM - 1) / kGemmBM), 256, 0, s>>>(
+          rows, ld, cols, n_rows, m, a_inv, amax, tau_sel, tau_brk, gamma, flags, gmax_bits, n_amb, nullptr, nullptr);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaMemcpyAsync(host, scratch, sizeof(host), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  cudaFree(scratch);
+  if (e != cudaSuccess) {
+    set_error("mtp_grade_rows: %s", cudaGetErrorString(e));
+    return MTP_ERR_CUDA;
+  }
+  double g;
+  std::memcpy(&g, &host[0], sizeof(g));
+  if (gamma_max) *gamma_max = g;
+  if (n_ambiguous) *n_ambiguous = (int64_t)host[1];
+  if (!std::isfinite(g)) {
+    set_error("mtp_grade_rows: non-finite grade");
+    return MTP_ERR_NONFINITE;
+  }
+  return g > tau_brk ? MTP_STATUS_BREAK : MTP_OK;
 }

@@ -95,6 +95,11 @@ __global__ void species_check_kernel(const int32_t* __restrict__ z, int64_t n, i
 
 using namespace mtp;
 
+namespace mtp {
+// Below this many atoms an untuned handle takes the warp-per-atom kernel.
+constexpr int64_t kTeamDefaultAtoms = 8192;
+}  // namespace mtp
+
 extern "C" {
 
 const char* mtp_last_error(void) { return g_err; }
@@ -478,6 +483,19 @@ int mtp_compute_efv(mtp_handle* h, const mtp_nlist* nl, const double* x, const i
     MTP_TRY_CUDA(cudaGetLastError());
   }
   const int64_t chunk = chunk_atoms > 0 ? chunk_atoms : n;
+  // energy/force kernel: one thread per atom, or one warp per atom (small
+  // systems); forced by mtp_set_efv_variant, else the tuned choice for this
+  // size (mtp_efv_tune), else by size
+  int variant = h->efv_variant;
+  if (variant == 0) {
+    const int bucket = std::min(63, (int)std::floor(std::log2((double)std::max<int64_t>(n, 1))));
+    variant = h->tuned[precision == MTP_MIXED ? 1 : 0][bucket];
+    if (variant == 0) variant = n <= kTeamDefaultAtoms ? 2 : 1;
+    if (variant == 2 && h->ops->split_comps > 0) variant = 1;
+  } else if (variant == 2 && h->ops->split_comps > 0) {
+    set_error("mtp_compute_efv: level %d runs only one thread per atom", h->level);
+    return MTP_ERR_UNSUPPORTED;
+  }
   if (h->ops->split_comps > 0 && n > 0) {
     // moment/adjoint scratch of the split kernels (levels with an interpreted
     // contraction), bounded by the chunk as the paper's chunk size bounds memory
@@ -490,12 +508,75 @@ int mtp_compute_efv(mtp_handle* h, const mtp_nlist* nl, const double* x, const i
   for (int64_t b = 0; b < n; b += chunk) {
     a.atom_begin = b;
     a.atom_end = b + chunk < n ? b + chunk : n;
-    int rc = h->ops->efv(a, precision, dtheta != nullptr, s);
+    int rc = variant == 2 ? h->ops->team(a, precision, dtheta != nullptr, s)
+                          : h->ops->efv(a, precision, dtheta != nullptr, s);
     if (rc != MTP_OK) return rc;
   }
   if (precision == MTP_MIXED) {
     forces_to_fp64_kernel<<<(unsigned)((3 * n + 255) / 256), 256, 0, s>>>(a.forces_f, 3 * n, forces);
     MTP_TRY_CUDA(cudaGetLastError());
+  }
+  return MTP_OK;
+}
+
+int mtp_set_efv_variant(mtp_handle* h, int32_t variant) {
+  if (!h || variant < 0 || variant > 2) {
+    set_error("mtp_set_efv_variant: variant must be 0 (auto), 1 (thread per atom) or 2 (warp per atom)");
+    return MTP_ERR_ARG;
+  }
+  if (variant == 2 && h->ops->split_comps > 0) {
+    set_error("mtp_set_efv_variant: level %d runs only one thread per atom", h->level);
+    return MTP_ERR_UNSUPPORTED;
+  }
+  h->efv_variant = variant;
+  return MTP_OK;
+}
+
+int mtp_efv_tune(mtp_handle* h, const mtp_nlist* nl, const double* x, const int32_t* z, int64_t n,
+                 const double* cell, int32_t precision, int32_t* chosen, float* ms_out, void* stream) {
+  if (!h || !nl || n <= 0 || (precision != MTP_FP64 && precision != MTP_MIXED)) {
+    set_error("mtp_efv_tune: invalid argument");
+    return MTP_ERR_ARG;
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  const int saved = h->efv_variant;
+  const int n_var = h->ops->split_comps > 0 ? 1 : 2;
+  double* buf = nullptr;
+  MTP_TRY_CUDA(cudaMalloc(&buf, sizeof(double) * (4 * (size_t)n + 8)));
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  float best = 0.f, t[2] = {0.f, 0.f};
+  int win = 1, rc = MTP_OK;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) rc = MTP_ERR_CUDA;
+  for (int v = 1; rc == MTP_OK && v <= n_var; ++v) {
+    h->efv_variant = v;
+    for (int rep = 0; rc == MTP_OK && rep < 4; ++rep) {   // one warm-up, three timed
+      if (rep == 1 && cudaEventRecord(e0, s) != cudaSuccess) rc = MTP_ERR_CUDA;
+      if (rc == MTP_OK)
+        rc = mtp_compute_efv(h, nl, x, z, n, cell, precision, 0, buf, buf + n, buf + 4 * n, buf + 4 * n + 6, nullptr,
+                             stream);
+    }
+    if (rc == MTP_OK && (cudaEventRecord(e1, s) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+                         cudaEventElapsedTime(&t[v - 1], e0, e1) != cudaSuccess))
+      rc = MTP_ERR_CUDA;
+    if (rc == MTP_OK && (v == 1 || t[v - 1] < best)) {
+      best = t[v - 1];
+      win = v;
+    }
+  }
+  h->efv_variant = saved;
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  cudaFree(buf);
+  if (rc != MTP_OK) {
+    if (rc == MTP_ERR_CUDA) set_error("mtp_efv_tune: timing failed");
+    return rc;
+  }
+  const int bucket = std::min(63, (int)std::floor(std::log2((double)n)));
+  h->tuned[precision == MTP_MIXED ? 1 : 0][bucket] = (int8_t)win;
+  if (chosen) *chosen = win;
+  if (ms_out) {
+    ms_out[0] = t[0] / 3.f;
+    ms_out[1] = n_var > 1 ? t[1] / 3.f : 0.f;
   }
   return MTP_OK;
 }

@@ -99,6 +99,7 @@ struct LevelEntry {
   BatchLaunch batch;
   TangentLaunch tangent;
   int split_comps;   // components per atom of the EfvArgs::mbuf scratch (0: the level needs none)
+  EfvLaunch team;    // warp-per-atom energy/force kernel (levels without component groups)
 };
 
 const LevelEntry* find_level(int level);
@@ -131,6 +132,8 @@ struct mtp_handle {
   mtp::DevBuf forces_f;  // FP32 force accumulator (mixed path)
   mtp::DevBuf grade;     // grade scratch: counters, row maxima, column sums, FP64 basis rows
   mtp::DevBuf mbuf;      // moment/adjoint scratch of levels whose contraction is interpreted
+  int efv_variant = 0;   // 0: tuned or by size, 1: thread per atom, 2: warp per atom
+  int8_t tuned[2][64] = {};   // [precision][floor(log2 N)]: 0 untuned, else the faster variant
 };
 
 struct mtp_nlist {

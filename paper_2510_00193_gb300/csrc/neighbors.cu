@@ -50,11 +50,12 @@ static double unordered_bits(unsigned long long b) {
 
 __global__ void wrap_kernel(const double* __restrict__ x, int64_t n, NbrGeom g, double* __restrict__ sw,
                             int* __restrict__ wrapcnt, unsigned long long* __restrict__ extent,
-                            float4* __restrict__ xw) {
+                            float4* __restrict__ xw, int* __restrict__ status) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   unsigned long long lo[3] = {~0ull, ~0ull, ~0ull}, hi[3] = {0ull, 0ull, 0ull};
   if (i < n) {
     const double px = x[3 * i], py = x[3 * i + 1], pz = x[3 * i + 2];
+    if (!isfinite(px) || !isfinite(py) || !isfinite(pz)) atomicCAS(status, 0, MTP_ERR_NONFINITE);
     double sv[3];
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
@@ -280,18 +281,17 @@ int build_neighbors(mtp_nlist* nl, const double* x, int64_t n, const double* cel
   MTP_TRY_CUDA(cudaMemsetAsync(status, 0, sizeof(int), stream));
   const unsigned long long ext_init[6] = {~0ull, 0ull, ~0ull, 0ull, ~0ull, 0ull};
   MTP_TRY_CUDA(cudaMemcpyAsync(extent, ext_init, sizeof(ext_init), cudaMemcpyHostToDevice, stream));
-  if (n > 0) wrap_kernel<<<blocks, T, 0, stream>>>(x, n, g, sw, wrapcnt, extent, xw);
+  if (n > 0) wrap_kernel<<<blocks, T, 0, stream>>>(x, n, g, sw, wrapcnt, extent, xw, status);
   MTP_TRY_CUDA(cudaGetLastError());
   unsigned long long ext_bits[6];
+  int wrap_status = 0;
   MTP_TRY_CUDA(cudaMemcpyAsync(ext_bits, extent, sizeof(ext_bits), cudaMemcpyDeviceToHost, stream));
+  MTP_TRY_CUDA(cudaMemcpyAsync(&wrap_status, status, sizeof(int), cudaMemcpyDeviceToHost, stream));
   MTP_TRY_CUDA(cudaStreamSynchronize(stream));
-  if (n > 0)
-    for (int k = 0; k < 6; ++k)
-      if (!std::isfinite(unordered_bits(ext_bits[k]))) {
-        // a NaN or infinite position reaches the extent of its fractional coordinate
-        set_error("mtp_build_neighbors: non-finite position");
-        return MTP_ERR_NONFINITE;
-      }
+  if (wrap_status == MTP_ERR_NONFINITE) {
+    set_error("mtp_build_neighbors: non-finite position");
+    return MTP_ERR_NONFINITE;
+  }
   int64_t nbins = 1;
   for (int k = 0; k < 3; ++k) {
     if (g.pbc[k]) {

@@ -697,3 +697,39 @@ def test_berendsen_ideal_gas_relaxes_to_the_ideal_gas_volume():
     assert np.array_equal(v, v0)
     assert abs(np.linalg.det(cell)) == pytest.approx(v_star, rel=1e-6)
     assert pr[-1] == pytest.approx(p_target, rel=1e-6)
+
+
+def test_independent_columns_on_known_rank():
+    """A 12 x 6 matrix whose columns 4 and 5 are combinations of columns 0-2:
+    four columns are independent, and every dropped column is reproduced by
+    the kept ones to rounding."""
+    g = np.random.default_rng(5)
+    a = g.normal(size=(12, 6))
+    a[:, 4] = 2.0 * a[:, 0] - a[:, 2]
+    a[:, 5] = 0.5 * a[:, 1] + 3.0 * a[:, 0]
+    cols = O.independent_columns(a)
+    assert len(cols) == 4
+    for k in set(range(6)) - set(cols):
+        coef, *_ = np.linalg.lstsq(a[:, cols], a[:, k], rcond=None)
+        assert np.abs(a[:, cols] @ coef - a[:, k]).max() <= 1e-12 * np.abs(a[:, k]).max()
+
+
+def test_parameter_gradient_has_the_radial_mixing_relations():
+    """dE/dtheta of any set of configurations satisfies n_mu (n_mu + 1) / 2
+    exact linear relations: E is unchanged to first order when f_mu gains a
+    multiple of f_nu (nu <= mu; nu = mu is a scaling) and xi compensates.
+    At level 8 (n_mu = 2) the independent columns of a pool of 40 strained
+    16-atom BCC cells number n_params - 3."""
+    model = O.load_model(pot_file("bcc-l8-s1"))
+    rows = []
+    g = synth.rng(31, 61)
+    for k in range(40):
+        st = synth.crystal("bcc", (2, 2, 2), 3.16, 0.05, 1, 31, sub=100 + k)
+        d = np.diag(1.0 + g.uniform(-0.02, 0.02, size=3))
+        x, cell = st.x @ d, st.cell @ d
+        out = O.evaluate(model, x, st.z, cell, O.neighbor_list(x, cell, st.pbc, model.pot.r_cut),
+                         want=("e", "dtheta"))
+        rows.append(np.concatenate([out["dE_ds"], out["dE_dc"].ravel(), out["dE_dxi"]]))
+    rows = np.array(rows)
+    n_mu = model.pot.radial.shape[0]
+    assert len(O.independent_columns(rows)) == rows.shape[1] - n_mu * (n_mu + 1) // 2
