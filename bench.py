@@ -301,6 +301,40 @@ def time_tc_kernel(P, torch, rows=262144, reps=5):
             "frac": flops / (ms * 1e-3) / 1e12 / peak}
 
 
+def run_small(P, torch, args):
+    """Small systems (the paper's block-parallel regime, ~2,000 atoms per GPU):
+    level-16 BCC boxes of 2,000 and 16,000 atoms (3 species, sigma 0.08 A),
+    mixed precision, one thread per atom against one warp per atom, and the
+    tuner's choice."""
+    import synth
+    pot = P.Potential.from_file(os.path.join(ROOT, "potentials", POTENTIAL + ".json"))
+    out = {}
+    for cells in (10, 20):
+        st = synth.crystal("bcc", (cells,) * 3, 3.16, 0.08, 3, 2)
+        x = torch.tensor(st.x, device="cuda")
+        z = torch.tensor(st.z, dtype=torch.int32, device="cuda")
+        nl = P.mtp_build_neighbors(pot, x, st.cell, st.pbc)
+        res = {}
+        for name, variant in (("thread_per_atom", 1), ("warp_per_atom", 2)):
+            P.mtp_set_efv_variant(pot, variant)
+            o = P.mtp_compute_efv(pot, nl, x, z, st.cell, precision=P.MTP_MIXED)
+            for _ in range(5):
+                P.mtp_compute_efv(pot, nl, x, z, st.cell, precision=P.MTP_MIXED, out=o)
+            reps = 50
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            for _ in range(reps):
+                P.mtp_compute_efv(pot, nl, x, z, st.cell, precision=P.MTP_MIXED, out=o)
+            e1.record()
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1) / reps
+            res[name] = {"ms": ms, "atom_steps_per_s": st.n / (ms * 1e-3)}
+        P.mtp_set_efv_variant(pot, 0)
+        res["tuner"] = P.mtp_efv_tune(pot, nl, x, z, st.cell, precision=P.MTP_MIXED)
+        out["%d_atoms" % st.n] = res
+    return out
+
+
 def run_batch(P, torch, args):
     """4096 periodic configurations of 8..256 atoms (2 species, level 16,
     random triclinic cells at 0.085 atoms/A^3, 1.9 A minimum separation):
@@ -731,6 +765,7 @@ def run_ours(args):
 
     grade = None if args.no_grade else run_grade(P, torch, args)
     batch = None if args.no_batch else run_batch(P, torch, args)
+    small = None if args.no_batch else run_small(P, torch, args)
     diff = None if args.no_diff else run_diff(P, torch, args)
     md = None
     md_graded = None
@@ -787,6 +822,7 @@ def run_ours(args):
                     "bytes_per_atom": bytes_atom, "peak_source": peak_src},
             "grade": grade,
             "batch": batch,
+            "small_systems": small,
             "differentiation": diff,
             "md": md,
             "md_with_grade": md_graded,

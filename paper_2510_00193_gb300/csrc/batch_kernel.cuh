@@ -59,7 +59,8 @@ __global__ void __launch_bounds__(256) batch_kernel(const BatchArgs b) {
 template <class LV, class R, bool DTHETA>
 int batch_launch_typed(const BatchArgs& b, int threads, cudaStream_t stream) {
   const int SS = b.base.n_species * b.base.n_species;
-  const size_t bytes = efv_smem_bytes<R, LV::NMU, DTHETA>(SS, b.base.n_q, b.base.m);
+  const size_t bytes = ((efv_smem_bytes<R, LV::NMU, DTHETA>(SS, b.base.n_q, b.base.m) + 15) & ~size_t(15)) +
+                       efv_acc_bytes<R, LV::NMU, DTHETA>(b.base.n_species, b.base.n_q, threads);
   auto kern = batch_kernel<LV, R, DTHETA>;
   if (bytes > 48 * 1024) {
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);

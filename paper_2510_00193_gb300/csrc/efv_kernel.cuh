@@ -317,6 +317,30 @@ __host__ __device__ __forceinline__ size_t efv_smem_bytes(int SS, int nq, int m)
   return efv_red_offset<R, NMU, DTHETA>(SS, nq, m) + sizeof(double) * 8 * kMaxWarps + sizeof(int) * kMaxSpecies;
 }
 
+// Mixed path with DTHETA: each thread's dE/dc accumulators [zj][mu][k] in
+// shared memory, strided by the block size ([entry][thread], conflict-free),
+// after the areas above.  (As a thread-private array indexed with the
+// run-time n_q they lived in local memory, whose lines the batch kernel wrote
+// back to DRAM.)  The FP64 path keeps the thread-private array.
+template <class R, int NMU, bool DTHETA>
+__host__ __device__ __forceinline__ size_t efv_acc_bytes(int S, int nq, int threads) {
+  return (DTHETA && sizeof(R) == 4 && S <= 4) ? sizeof(R) * (size_t)S * NMU * nq * threads : 0;
+}
+
+__device__ __forceinline__ uint32_t dynamic_smem_size() {
+  uint32_t r;
+  asm("mov.u32 %0, %%dynamic_smem_size;" : "=r"(r));
+  return r;
+}
+
+// Accumulator array with a stride: thread-private (stride 1) or a thread's
+// column of the shared [entry][thread] array.
+template <class R> struct AccView {
+  R* p;
+  int stride;
+  __device__ __forceinline__ R& operator[](int t) const { return p[t * stride]; }
+};
+
 // Shared-memory view: radial coefficients [zi*S+zj][mu][k] (odd stride: the
 // species-pair blocks fall on distinct banks), xi, and with DTHETA the
 // per-block gradient accumulators.
@@ -326,6 +350,7 @@ struct EfvShared {
   R* xi;
   R* dc;      // [SS][NMU][nq]
   R* dxi;     // [m]
+  R* acc;     // mixed DTHETA: per-thread dE/dc accumulators [S NMU nq][blockDim], or null
   double* red;
   int* cnt;   // [S]
   int S, SS, nq, cstride, m;
@@ -343,6 +368,12 @@ struct EfvShared {
     dxi = dc + (DTHETA ? SS * NMU * nq : 0);
     red = reinterpret_cast<double*>(raw + efv_red_offset<R, NMU, DTHETA>(SS, nq, m));
     cnt = reinterpret_cast<int*>(red + 8 * kMaxWarps);
+    acc = nullptr;
+    if (DTHETA && sizeof(R) == 4 && S <= 4) {
+      const size_t off = (efv_smem_bytes<R, NMU, DTHETA>(SS, nq, m) + 15) & ~size_t(15);
+      if ((size_t)dynamic_smem_size() >= off + efv_acc_bytes<R, NMU, DTHETA>(S, nq, blockDim.x))
+        acc = reinterpret_cast<R*>(raw + off);
+    }
     const R* radial_src;
     const R* xi_src;
     if constexpr (sizeof(R) == 8) {
@@ -415,7 +446,8 @@ template <class LV, class R, bool DTHETA, int G, bool CLOSE64 = false>
 __device__ __forceinline__ void adjoint_sweep(const EfvArgs& a, const EfvShared<R, LV::NMU, DTHETA>& sm,
                                               const PairGeom<R>& geom, const double* cell64, int zi, int64_t beg,
                                               int64_t end,
-                                              const R* D, R& fx, R& fy, R& fz, R* w, R* acc, bool own_acc) {
+                                              const R* D, R& fx, R& fy, R& fz, R* w, AccView<R> acc,
+                                              bool own_acc) {
   constexpr int NMU = LV::NMU;
   PairStream<R> ps;
   int32_t j, img;
@@ -460,13 +492,16 @@ __device__ __forceinline__ void adjoint_sweep(const EfvArgs& a, const EfvShared<
         mu_hi = LV::GROUP_MU_HI[G];
       }
       if (own_acc) {
-        R* dst = acc + zj * NMU * sm.nq;
+        const int base = zj * NMU * sm.nq;
 #pragma unroll
         for (int mu = 0; mu < NMU; ++mu) {
           if (mu < mu_lo || mu >= mu_hi) continue;
 #pragma unroll
           for (int kk = 0; kk < kMaxQ; ++kk)
-            if (kk < sm.nq) dst[mu * sm.nq + kk] = fmadd(q[kk], Smu[mu], dst[mu * sm.nq + kk]);
+            if (kk < sm.nq) {
+              R& d = acc[base + mu * sm.nq + kk];
+              d = fmadd(q[kk], Smu[mu], d);
+            }
         }
       } else {
         R* dst = sm.dc + (zi * sm.S + zj) * NMU * sm.nq;
@@ -549,8 +584,10 @@ __device__ __forceinline__ void efv_atom(const EfvArgs& a, const EfvShared<R, LV
   // per atom (per-pair shared atomics collide heavily between lanes)
   // (packed [zj][mu][k] with the runtime n_q, so only S NMU n_q entries are touched)
   constexpr int kAccS = 4;
-  const bool own_acc = DTHETA && sm.S <= kAccS;
-  R acc[DTHETA ? kAccS * NMU * kMaxQ : 1];
+  R acc_local[(DTHETA && sizeof(R) == 8) ? kAccS * NMU * kMaxQ : 1];
+  const AccView<R> acc = (sizeof(R) == 4) ? AccView<R>{sm.acc ? sm.acc + threadIdx.x : nullptr, (int)blockDim.x}
+                                          : AccView<R>{acc_local, 1};
+  const bool own_acc = DTHETA && sm.S <= kAccS && acc.p != nullptr;
   if (own_acc) {
     for (int t = 0; t < sm.S * NMU * sm.nq; ++t) acc[t] = R(0);
   }
@@ -740,8 +777,10 @@ __global__ void __launch_bounds__(kEfvThreads) split_adjoint_kernel(const EfvArg
     const R* buf = static_cast<const R*>(a.mbuf) + (size_t)LV::NCOMP * n + (active ? t : 0);
     R fx = R(0), fy = R(0), fz = R(0);
     constexpr int kAccS = 4;
-    const bool own_acc = DTHETA && sm.S <= kAccS;
-    R acc[DTHETA ? kAccS * NMU * kMaxQ : 1];
+    R acc_local[(DTHETA && sizeof(R) == 8) ? kAccS * NMU * kMaxQ : 1];
+    const AccView<R> acc = (sizeof(R) == 4) ? AccView<R>{sm.acc ? sm.acc + threadIdx.x : nullptr, (int)blockDim.x}
+                                            : AccView<R>{acc_local, 1};
+    const bool own_acc = DTHETA && sm.S <= kAccS && acc.p != nullptr;
     if (own_acc) {
       for (int u = 0; u < sm.S * NMU * sm.nq; ++u) acc[u] = R(0);
     }
@@ -789,7 +828,8 @@ int efv_split_launch(const EfvArgs& a, cudaStream_t stream) {
   if (n <= 0) return MTP_OK;
   const unsigned grid = (unsigned)((n + kEfvThreads - 1) / kEfvThreads);
   const size_t b0 = efv_smem_bytes<R, LV::NMU, false>(SS, a.n_q, a.m);
-  const size_t b1 = efv_smem_bytes<R, LV::NMU, DTHETA>(SS, a.n_q, a.m);
+  const size_t b1 = ((efv_smem_bytes<R, LV::NMU, DTHETA>(SS, a.n_q, a.m) + 15) & ~size_t(15)) +
+                    efv_acc_bytes<R, LV::NMU, DTHETA>(a.n_species, a.n_q, kEfvThreads);
   int rc;
   if ((rc = set_smem(split_moments_kernel<LV, R>, b0)) != MTP_OK) return rc;
   if ((rc = set_smem(split_contract_kernel<LV, R, DTHETA>, b1)) != MTP_OK) return rc;
@@ -811,7 +851,8 @@ int efv_launch_typed(const EfvArgs& a, cudaStream_t stream) {
     if (a.mbuf) return efv_split_launch<LV, R, DTHETA>(a, stream);
   }
   const int SS = a.n_species * a.n_species;
-  const size_t bytes = efv_smem_bytes<R, LV::NMU, DTHETA>(SS, a.n_q, a.m);
+  const size_t bytes = ((efv_smem_bytes<R, LV::NMU, DTHETA>(SS, a.n_q, a.m) + 15) & ~size_t(15)) +
+                       efv_acc_bytes<R, LV::NMU, DTHETA>(a.n_species, a.n_q, kEfvThreads);
   auto kern = efv_kernel<LV, R, DTHETA>;
   if (bytes > 48 * 1024) {
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);

@@ -97,7 +97,7 @@ using namespace mtp;
 
 namespace mtp {
 // Below this many atoms an untuned handle takes the warp-per-atom kernel.
-constexpr int64_t kTeamDefaultAtoms = 8192;
+constexpr int64_t kTeamDefaultAtoms = 2048;
 }  // namespace mtp
 
 extern "C" {
