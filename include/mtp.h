@@ -152,7 +152,7 @@ int mtp_compute_efv(mtp_handle* h, const mtp_nlist* nl, const double* x_dev, con
  *      Sec. 2.1, Table 1, Sec. 4); levels up to 16 (levels 18 and 20 run one
  *      thread per atom: MTP_ERR_UNSUPPORTED);
  *   0 (default): the variant mtp_efv_tune measured faster for the atom count's
- *      power-of-two size class, else warp per atom up to 8192 atoms. */
+ *      power-of-two size class, else warp per atom up to 2048 atoms. */
 int mtp_set_efv_variant(mtp_handle* h, int32_t variant);
 /* Times both variants on this configuration (one warm-up and three timed
  * evaluations each, CUDA events on `stream`) and records the faster for its
