@@ -33,7 +33,7 @@ FP32_LANES = 128
 # DRAM read + write per atom of efv_kernel<MtpLevel16, float, 0> from the
 # latest ncu capture in profiles/efv_kernel_bcc70_l16_mixed.md (686,000 atoms;
 # traffic scales with the atom count).  Set to None whenever that kernel changes.
-EFV_TRAFFIC_BYTES_PER_ATOM = (185.553664e6 + 210.851072e6) / 686000
+EFV_TRAFFIC_BYTES_PER_ATOM = None
 
 
 def _peaks():
@@ -303,9 +303,9 @@ def time_tc_kernel(P, torch, rows=262144, reps=5):
 
 def run_small(P, torch, args):
     """Small systems (the paper's block-parallel regime, ~2,000 atoms per GPU):
-    level-16 BCC boxes of 2,000 and 16,000 atoms (3 species, sigma 0.08 A),
-    mixed precision, one thread per atom against one warp per atom, and the
-    tuner's choice."""
+    level-16 BCC boxes of 2,000 and 16,000 atoms (3 species, sigma 0.08 A) and
+    a level-20 FCC box of 2,048 atoms (4 species), mixed precision, one thread
+    per atom against one warp per atom, and the tuner's choice."""
     import synth
     pot = P.Potential.from_file(os.path.join(ROOT, "potentials", POTENTIAL + ".json"))
     out = {}
@@ -332,6 +332,31 @@ def run_small(P, torch, args):
         P.mtp_set_efv_variant(pot, 0)
         res["tuner"] = P.mtp_efv_tune(pot, nl, x, z, st.cell, precision=P.MTP_MIXED)
         out["%d_atoms" % st.n] = res
+    # level 20 (interpreted contraction): 2,048-atom FCC, 4 species, the
+    # differentiation recipe at small size
+    pot20 = P.Potential.from_file(os.path.join(ROOT, "potentials", "fcc-l20-s4.json"))
+    st = synth.crystal("fcc", (8, 8, 8), 3.6, 0.1, 4, 3)
+    x = torch.tensor(st.x, device="cuda")
+    z = torch.tensor(st.z, dtype=torch.int32, device="cuda")
+    nl = P.mtp_build_neighbors(pot20, x, st.cell, st.pbc)
+    res = {}
+    for name, variant in (("thread_per_atom_three_kernels", 1), ("warp_per_atom", 2)):
+        P.mtp_set_efv_variant(pot20, variant)
+        o = P.mtp_compute_efv(pot20, nl, x, z, st.cell, precision=P.MTP_MIXED)
+        for _ in range(3):
+            P.mtp_compute_efv(pot20, nl, x, z, st.cell, precision=P.MTP_MIXED, out=o)
+        reps = 20
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            P.mtp_compute_efv(pot20, nl, x, z, st.cell, precision=P.MTP_MIXED, out=o)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / reps
+        res[name] = {"ms": ms, "atom_steps_per_s": st.n / (ms * 1e-3)}
+    P.mtp_set_efv_variant(pot20, 0)
+    res["tuner"] = P.mtp_efv_tune(pot20, nl, x, z, st.cell, precision=P.MTP_MIXED)
+    out["level20_%d_atoms" % st.n] = res
     return out
 
 

@@ -149,16 +149,16 @@ int mtp_compute_efv(mtp_handle* h, const mtp_nlist* nl, const double* x_dev, con
  *      systems; paper Sec. 2.1, Table 1);
  *   2: one warp per centre atom, the warp's lanes sharing the atom's pairs
  *      (the block-parallel variant for small systems and high levels, paper
- *      Sec. 2.1, Table 1, Sec. 4); levels up to 16 (levels 18 and 20 run one
- *      thread per atom: MTP_ERR_UNSUPPORTED);
+ *      Sec. 2.1, Table 1, Sec. 4); at levels 18 and 20 the warp also shares
+ *      the interpreted contraction, level by level of its records;
  *   0 (default): the variant mtp_efv_tune measured faster for the atom count's
  *      power-of-two size class, else warp per atom up to 2048 atoms. */
 int mtp_set_efv_variant(mtp_handle* h, int32_t variant);
 /* Times both variants on this configuration (one warm-up and three timed
  * evaluations each, CUDA events on `stream`) and records the faster for its
  * precision and power-of-two size class in the handle.  chosen (HOST,
- * nullable): 1 or 2; ms (HOST [2], nullable): mean ms per evaluation of each
- * (0 for a variant the level does not have).  Allocates scratch outputs for
+ * nullable): 1 or 2; ms (HOST [2], nullable): mean ms per evaluation of
+ * each.  Allocates scratch outputs for
  * the call; synchronises `stream`. */
 int mtp_efv_tune(mtp_handle* h, const mtp_nlist* nl, const double* x_dev, const int32_t* z_dev, int64_t n_atoms,
                  const double* cell, int32_t precision, int32_t* chosen, float* ms, void* stream);

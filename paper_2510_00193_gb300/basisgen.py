@@ -601,9 +601,11 @@ def emit_contract(lv: Level):
     dag = lv.dag
     L = []
     ind = "    "
-    L.append("  template <class R, bool WANT_B>")
-    L.append("  __device__ __forceinline__ static R contract(const R* __restrict__ M, "
-             "const typename ScalarOf<R>::T* __restrict__ xi, R* __restrict__ D, R* __restrict__ B) {")
+    # M: the moment components, indexed M[c] (an array, or a strided view of them in shared memory)
+    # B: where the basis values go when WANT_B: an array (B[a] = value) or a sink called as B(a, value)
+    L.append("  template <class R, bool WANT_B, class MV = const R*, class BV = R*>")
+    L.append("  __device__ __forceinline__ static R contract(MV M, "
+             "const typename ScalarOf<R>::T* __restrict__ xi, R* __restrict__ D, BV B) {")
     L.append(ind + "(void)B;")
     # forward
     def comp_ref(n, K):
@@ -646,7 +648,7 @@ def emit_contract(lv: Level):
     L.append(ind + "R E = R(0);")
     for a, b in enumerate(lv.bases):
         L.append(ind + "const R B%d = %s;" % (a, " * ".join("G%d" % k for k in b)))
-        L.append(ind + "if (WANT_B) B[%d] = B%d;" % (a, a))
+        L.append(ind + "if (WANT_B) store_basis(B, %d, B%d);" % (a, a))
         L.append(ind + "E = fmadd(R(xi[%d]), B%d, E);" % (a, a))
     # reverse: dE/dG
     gbar = defaultdict(list)
@@ -777,14 +779,44 @@ def emit_contract_program(lv: Level):
     for a_, bas in enumerate(lv.bases):
         starts.append(len(prog))
         prog += [1, boff + a_, len(bas)] + [goff + k for k in bas]
+    # dependency levels of the records (for the warp-parallel interpreter):
+    # a record's level is one more than the highest level among the records
+    # that produce its inputs (moments and the constant 1 are level 0)
+    vlevel = {}
+    rlevel = []
+    for st in starts:
+        typ, dst, cnt = prog[st], prog[st + 1], prog[st + 2]
+        if typ == 0:
+            ins = [prog[st + 3 + 3 * t] for t in range(cnt)] + [prog[st + 4 + 3 * t] for t in range(cnt)]
+        else:
+            ins = [prog[st + 3 + t] for t in range(cnt)]
+        lev = 1 + max(vlevel.get(v, 0) for v in ins)
+        vlevel[dst] = lev
+        rlevel.append(lev)
+    nlev = max(rlevel)
+    order = sorted(range(len(starts)), key=lambda r: (rlevel[r], r))
+    level_off = [0] * (nlev + 1)
+    for r in order:
+        level_off[rlevel[r]] += 1
+    for k in range(1, nlev + 1):
+        level_off[k] += level_off[k - 1]
     L = []
     nm = "L%d" % lv.level
     L.append("  static constexpr int NVALUES = %d, ONE = %d, BOFF = %d, NRECORDS = %d;" % (nv, one, boff, len(starts)))
+    L.append("  static constexpr int NLEVELS = %d;   // dependency levels of the records" % nlev)
     L.append("  template <class R, bool WANT_B>")
     L.append("  __device__ static R contract(const R* __restrict__ M, const typename ScalarOf<R>::T* __restrict__ xi, "
              "R* __restrict__ D, R* __restrict__ B) {")
     L.append("    return interpret_contract<R, WANT_B, NCOMP, NVALUES, ONE, BOFF, NBASIS, NRECORDS>("
              "kProg%s, kStarts%s, M, xi, D, B);" % (nm, nm))
+    L.append("  }")
+    L.append("  // one warp: V, A shared arrays of NVALUES (V[0, NCOMP) = moments on entry, A[0, NCOMP) = dE/dM on")
+    L.append("  // return); the records of each dependency level are spread over the lanes")
+    L.append("  template <class R, bool WANT_B, class BV>")
+    L.append("  __device__ static R contract_warp(R* V, R* A, const typename ScalarOf<R>::T* __restrict__ xi, BV B, "
+             "int lane) {")
+    L.append("    return interpret_values_warp<R, WANT_B, NCOMP, NVALUES, ONE, BOFF, NBASIS, NLEVELS>("
+             "kProg%s, kStarts%s, kLevelOrder%s, kLevelOff%s, V, A, xi, B, lane);" % (nm, nm, nm, nm))
     L.append("  }")
     L.append("  // V[0, NCOMP) = moments on entry, A[0, NCOMP) = dE/dM on return (arrays of NVALUES)")
     L.append("  template <class R, bool WANT_B>")
@@ -794,7 +826,9 @@ def emit_contract_program(lv: Level):
              "kProg%s, kStarts%s, V, A, xi, B);" % (nm, nm))
     L.append("  }")
     tables = ["__device__ const int32_t kProg%s[] = {%s};" % (nm, ",".join(str(v) for v in prog)),
-              "__device__ const int32_t kStarts%s[] = {%s};" % (nm, ",".join(str(v) for v in starts))]
+              "__device__ const int32_t kStarts%s[] = {%s};" % (nm, ",".join(str(v) for v in starts)),
+              "__device__ const int32_t kLevelOrder%s[] = {%s};" % (nm, ",".join(str(v) for v in order)),
+              "__device__ const int32_t kLevelOff%s[] = {0,%s};" % (nm, ",".join(str(v) for v in level_off[1:]))]
     return L, tables
 
 
@@ -819,6 +853,10 @@ def emit_groups(lv: Level):
                  "R* __restrict__ Dg) {" % g)
         L += ["    Dg[%d] = D[%d * ld];" % (c, c) for c in grp]
         L.append("  }")
+    for grp in lv.groups:
+        assert sorted(grp) == list(range(min(grp), max(grp) + 1)), "component groups are contiguous ranges"
+    L.append("  static constexpr int GROUP_C_LO[%d] = {%s};" % (ng, ", ".join(str(min(g)) for g in lv.groups)))
+    L.append("  static constexpr int GROUP_C_HI[%d] = {%s};" % (ng, ", ".join(str(max(g) + 1) for g in lv.groups)))
     mus = [sorted({lv.comps[c][0] for c in grp}) for grp in lv.groups]
     L.append("  static constexpr int GROUP_MU_LO[%d] = {%s};" % (ng, ", ".join(str(m[0]) for m in mus)))
     L.append("  static constexpr int GROUP_MU_HI[%d] = {%s};" % (ng, ", ".join(str(m[-1] + 1) for m in mus)))

@@ -21,7 +21,8 @@
 
 namespace mtp {
 
-constexpr int kEfvThreads = 128;
+constexpr int kEfvThreads = 128;       // split and warp-per-atom kernels
+constexpr int kEfvFusedThreads = 128;  // the fused one-thread-per-atom kernel
 
 __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll
@@ -335,6 +336,18 @@ __device__ __forceinline__ uint32_t dynamic_smem_size() {
 
 // Accumulator array with a stride: thread-private (stride 1) or a thread's
 // column of the shared [entry][thread] array.
+// Basis-value sink of the contraction: the warp's sum of basis value a
+// (lanes without an atom add zero) is added to the block's dE/dxi slot.
+template <class R> struct WarpBasisSink {
+  R* dxi;
+  int lane;
+  bool active;
+  __device__ __forceinline__ void operator()(int a, R v) const {
+    const R s = warp_sum_r(active ? v : R(0));
+    if (lane == 0) atomicAdd(dxi + a, s);
+  }
+};
+
 template <class R> struct AccView {
   R* p;
   int stride;
@@ -531,7 +544,7 @@ __device__ __forceinline__ void adjoint_sweep(const EfvArgs& a, const EfvShared<
 // and 20: 201 and 295 components) sweep the neighbours once per group, so
 // that a group's moments, then its adjoints, stay in registers; the full
 // vectors meet the interpreter once per atom.
-template <class LV, class R, bool DTHETA>
+template <class LV, class R, bool DTHETA, bool PHASE_SYNC = false>
 __device__ __forceinline__ void efv_atom(const EfvArgs& a, const EfvShared<R, LV::NMU, DTHETA>& sm, int64_t i,
                                          bool active, const R* cell, const double* cell64, double& e_i, R* w) {
   constexpr int NMU = LV::NMU;
@@ -562,19 +575,30 @@ __device__ __forceinline__ void efv_atom(const EfvArgs& a, const EfvShared<R, LV
     }
   }
   R D[LV::NCOMP];
-  R Bv[DTHETA ? LV::NBASIS : 1];
-  const R ei = LV::template contract<R, DTHETA>(M, sm.xi, D, Bv);
-  if (DTHETA) {
-    // warp sums of the basis values (dE/dxi), in R: the block accumulator is
-    // in R, and FP64 shuffles of 100+ values would occupy the FP64 pipe
-    // longer than the atoms' own work on the mixed path
-    const int lane = threadIdx.x & 31;
+  if constexpr (PHASE_SYNC) __syncthreads();
+  R ei;
+  if constexpr (DTHETA && LV::NGROUPS == 1) {
+    // dE/dxi: each basis value is summed across the warp as soon as the
+    // contraction forms it, so that none of them stays live through the
+    // reverse pass
+    ei = LV::template contract<R, true, const R*, WarpBasisSink<R>>(
+        M, sm.xi, D, WarpBasisSink<R>{sm.dxi, (int)(threadIdx.x & 31), active});
+  } else {
+    R Bv[DTHETA ? LV::NBASIS : 1];
+    ei = LV::template contract<R, DTHETA>(M, sm.xi, D, Bv);
+    if (DTHETA) {
+      // warp sums of the basis values (dE/dxi), in R: the block accumulator is
+      // in R, and FP64 shuffles of 100+ values would occupy the FP64 pipe
+      // longer than the atoms' own work on the mixed path
+      const int lane = threadIdx.x & 31;
 #pragma unroll
-    for (int t = 0; t < (DTHETA ? LV::NBASIS : 1); ++t) {
-      const R v = warp_sum_r(active ? Bv[t] : R(0));
-      if (lane == 0) atomicAdd(sm.dxi + t, v);
+      for (int t = 0; t < (DTHETA ? LV::NBASIS : 1); ++t) {
+        const R v = warp_sum_r(active ? Bv[t] : R(0));
+        if (lane == 0) atomicAdd(sm.dxi + t, v);
+      }
     }
   }
+  if constexpr (PHASE_SYNC) __syncthreads();
   e_i = active ? a.species_energy[zi] + (double)ei : 0.0;
   if (active) a.e_atom[i] = e_i;
 
@@ -662,7 +686,7 @@ __device__ __forceinline__ void efv_block_flush(const EfvShared<R, LV::NMU, DTHE
 }
 
 template <class LV, class R, bool DTHETA>
-__global__ void __launch_bounds__(kEfvThreads) efv_kernel(const EfvArgs a) {
+__global__ void __launch_bounds__(kEfvFusedThreads) efv_kernel(const EfvArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   EfvShared<R, LV::NMU, DTHETA> sm;
   sm.setup(a, smem_raw);
@@ -672,8 +696,10 @@ __global__ void __launch_bounds__(kEfvThreads) efv_kernel(const EfvArgs a) {
   double e_i = 0.0;
   R w[6] = {R(0), R(0), R(0), R(0), R(0), R(0)};
   const bool active = i < a.atom_end;
-  if (__any_sync(0xffffffffu, active))   // warp-uniform: whole warps without atoms skip the work
-    efv_atom<LV, R, DTHETA>(a, sm, active ? i : a.atom_begin, active, cell_of<R>(a), a.cell, e_i, w);
+  // the block's warps meet between the neighbour sweeps and the contraction,
+  // so that they run the same code at the same time (instruction cache); a
+  // warp without atoms runs the phases on zero pairs
+  efv_atom<LV, R, DTHETA, true>(a, sm, active ? i : a.atom_begin, active, cell_of<R>(a), a.cell, e_i, w);
   efv_block_flush<LV, R, DTHETA>(sm, e_i, w, a.e_total, a.virial, a.dtheta);
 }
 
@@ -852,7 +878,7 @@ int efv_launch_typed(const EfvArgs& a, cudaStream_t stream) {
   }
   const int SS = a.n_species * a.n_species;
   const size_t bytes = ((efv_smem_bytes<R, LV::NMU, DTHETA>(SS, a.n_q, a.m) + 15) & ~size_t(15)) +
-                       efv_acc_bytes<R, LV::NMU, DTHETA>(a.n_species, a.n_q, kEfvThreads);
+                       efv_acc_bytes<R, LV::NMU, DTHETA>(a.n_species, a.n_q, kEfvFusedThreads);
   auto kern = efv_kernel<LV, R, DTHETA>;
   if (bytes > 48 * 1024) {
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
@@ -863,8 +889,8 @@ int efv_launch_typed(const EfvArgs& a, cudaStream_t stream) {
   }
   const int64_t n = a.atom_end - a.atom_begin;
   if (n <= 0) return MTP_OK;
-  const unsigned grid = (unsigned)((n + kEfvThreads - 1) / kEfvThreads);
-  kern<<<grid, kEfvThreads, bytes, stream>>>(a);
+  const unsigned grid = (unsigned)((n + kEfvFusedThreads - 1) / kEfvFusedThreads);
+  kern<<<grid, kEfvFusedThreads, bytes, stream>>>(a);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) {
     set_error("efv kernel launch (level %d): %s", LV::LEVEL, cudaGetErrorString(e));

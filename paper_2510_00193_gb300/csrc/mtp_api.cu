@@ -491,12 +491,8 @@ int mtp_compute_efv(mtp_handle* h, const mtp_nlist* nl, const double* x, const i
     const int bucket = std::min(63, (int)std::floor(std::log2((double)std::max<int64_t>(n, 1))));
     variant = h->tuned[precision == MTP_MIXED ? 1 : 0][bucket];
     if (variant == 0) variant = n <= kTeamDefaultAtoms ? 2 : 1;
-    if (variant == 2 && h->ops->split_comps > 0) variant = 1;
-  } else if (variant == 2 && h->ops->split_comps > 0) {
-    set_error("mtp_compute_efv: level %d runs only one thread per atom", h->level);
-    return MTP_ERR_UNSUPPORTED;
   }
-  if (h->ops->split_comps > 0 && n > 0) {
+  if (h->ops->split_comps > 0 && n > 0 && variant == 1) {
     // moment/adjoint scratch of the split kernels (levels with an interpreted
     // contraction), bounded by the chunk as the paper's chunk size bounds memory
     const size_t bytes = 2 * (size_t)h->ops->split_comps * (size_t)std::min<int64_t>(chunk, n) *
@@ -524,10 +520,6 @@ int mtp_set_efv_variant(mtp_handle* h, int32_t variant) {
     set_error("mtp_set_efv_variant: variant must be 0 (auto), 1 (thread per atom) or 2 (warp per atom)");
     return MTP_ERR_ARG;
   }
-  if (variant == 2 && h->ops->split_comps > 0) {
-    set_error("mtp_set_efv_variant: level %d runs only one thread per atom", h->level);
-    return MTP_ERR_UNSUPPORTED;
-  }
   h->efv_variant = variant;
   return MTP_OK;
 }
@@ -540,7 +532,7 @@ int mtp_efv_tune(mtp_handle* h, const mtp_nlist* nl, const double* x, const int3
   }
   cudaStream_t s = (cudaStream_t)stream;
   const int saved = h->efv_variant;
-  const int n_var = h->ops->split_comps > 0 ? 1 : 2;
+  const int n_var = 2;
   double* buf = nullptr;
   MTP_TRY_CUDA(cudaMalloc(&buf, sizeof(double) * (4 * (size_t)n + 8)));
   cudaEvent_t e0 = nullptr, e1 = nullptr;

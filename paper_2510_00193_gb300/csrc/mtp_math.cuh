@@ -36,6 +36,13 @@ __host__ __device__ __forceinline__ Dual<S> fmadd(Dual<S> a, Dual<S> b, Dual<S> 
   return {fmadd(a.v, b.v, c.v), fmadd(a.v, b.t, fmadd(a.t, b.v, c.t))};
 }
 
+// Where the contraction puts basis value a: an array, or a sink object
+// called as sink(a, value) (which may reduce it at once).
+template <class R> __host__ __device__ __forceinline__ void store_basis(R* B, int a, R v) { B[a] = v; }
+template <class Sink, class R> __host__ __device__ __forceinline__ void store_basis(const Sink& B, int a, R v) {
+  B(a, v);
+}
+
 template <class R> __host__ __device__ __forceinline__ typename ScalarOf<R>::T value_of(R a) { return a; }
 template <class S> __host__ __device__ __forceinline__ S value_of(Dual<S> a) { return a.v; }
 
