@@ -160,6 +160,19 @@ struct PairStream {
     ++k;
     return true;
   }
+  // Branch-free step for the software-pipelined sweeps (beg < end): past the
+  // end it returns the last entry again, whose data are valid, and the caller
+  // discards what it computes from it.
+  __device__ __forceinline__ void step(const EfvArgs& a, const Geom& g, int32_t& j, int32_t& img,
+                                       typename Geom::Load& l) {
+    j = j1; img = im1; l = l1;
+    const int64_t k2 = k + 2 < end ? k + 2 : end - 1;
+    if (k + 1 < end) { j1 = j2; im1 = im2; }
+    l1 = g.fetch(a, j1);
+    j2 = __ldg(a.nbr_j + k2);
+    im2 = __ldg(a.nbr_img + k2);
+    ++k;
+  }
 };
 
 // Force accumulation: FP64 atomics on the FP64 path; FP32 atomics into the
@@ -183,28 +196,67 @@ __device__ __forceinline__ float rsqrt_r(float v) { return rsqrtf(v); }
 __device__ __forceinline__ double rsqrt_r(double v) { return rsqrt(v); }
 
 // Radial functions of one pair.  c points at the (zi, zj) block, [mu][k].
+// Radial coefficients in shared memory: per species pair (zi, zj) a block
+// [k][mu] with mu padded to whole 16-byte vectors (KS entries per k), so that
+// the NMU coefficients of one k arrive in one or two vector loads; successive
+// pair blocks start one vector apart beyond that, which spreads the lanes of
+// a warp (different neighbour species) over the banks.
+template <class C, int NMU>
+struct CoefLayout {
+  static constexpr int V = 16 / (int)sizeof(C);   // entries per 16-byte vector
+  static constexpr int KS = (NMU + V - 1) / V * V;
+  __host__ __device__ static constexpr int cstride(int nq) { return nq * KS + V; }
+  // shared index of c[mu][k] within a pair block
+  __host__ __device__ static constexpr int at(int mu, int k) { return k * KS + mu; }
+};
+
+template <class C, int NMU>
+__device__ __forceinline__ void load_coefs(const C* __restrict__ p, C (&v)[CoefLayout<C, NMU>::KS]) {
+  constexpr int KS = CoefLayout<C, NMU>::KS;
+  if constexpr (sizeof(C) == 4) {
+#pragma unroll
+    for (int g = 0; g < KS / 4; ++g) {
+      const float4 t = reinterpret_cast<const float4*>(p)[g];
+      v[4 * g] = t.x; v[4 * g + 1] = t.y; v[4 * g + 2] = t.z; v[4 * g + 3] = t.w;
+    }
+  } else {
+#pragma unroll
+    for (int g = 0; g < KS / 2; ++g) {
+      const double2 t = reinterpret_cast<const double2*>(p)[g];
+      v[2 * g] = t.x; v[2 * g + 1] = t.y;
+    }
+  }
+}
+
 // f_mu = cut^2 sum_k c T_k, df_mu/dr = scale cut^2 sum_k c T'_k - 2 cut sum_k c T_k,
 // with T_k(xi) the Chebyshev polynomials, xi = (r - mid) scale, cut = R_cut - r.
-template <class R, int NMU, bool DERIV, bool WANT_Q, class C>
-__device__ __forceinline__ void radial(const C* __restrict__ c, int nq, R r, R mid, R scale, R rcut, R* f,
+// c: the pair's coefficient block (CoefLayout).  NQ > 0 fixes n_q at compile
+// time (nq is then ignored).
+template <class R, int NMU, bool DERIV, bool WANT_Q, int NQ = 0, class C>
+__device__ __forceinline__ void radial(const C* __restrict__ c, int nq_rt, R r, R mid, R scale, R rcut, R* f,
                                        R* df, R* q) {
   // c holds scalar coefficients (C); R may be C or a dual number over C
+  using L = CoefLayout<C, NMU>;
+  const int nq = NQ > 0 ? NQ : nq_rt;
   const R x = (r - mid) * scale;
   const R cut = rcut - r;
   const R cut2 = cut * cut;
   R t0 = R(1), t1 = x, d0 = R(0), d1 = R(1);
   R A[NMU], Bd[NMU];
+  C cc[L::KS];
+  load_coefs<C, NMU>(c, cc);
 #pragma unroll
   for (int mu = 0; mu < NMU; ++mu) {
-    A[mu] = R(c[mu * nq]);
+    A[mu] = R(cc[mu]);
     Bd[mu] = R(0);
   }
   if (WANT_Q) q[0] = cut2;
   if (nq > 1) {
+    load_coefs<C, NMU>(c + L::KS, cc);
 #pragma unroll
     for (int mu = 0; mu < NMU; ++mu) {
-      A[mu] = fmadd(R(c[mu * nq + 1]), x, A[mu]);
-      if (DERIV) Bd[mu] = R(c[mu * nq + 1]);
+      A[mu] = fmadd(R(cc[mu]), x, A[mu]);
+      if (DERIV) Bd[mu] = R(cc[mu]);
     }
     if (WANT_Q) q[1] = x * cut2;
   }
@@ -213,11 +265,11 @@ __device__ __forceinline__ void radial(const C* __restrict__ c, int nq, R r, R m
     if (k < nq) {
       const R t2 = fmadd(R(2) * x, t1, -t0);
       const R d2 = fmadd(R(2) * x, d1, fmadd(R(2), t1, -d0));
+      load_coefs<C, NMU>(c + k * L::KS, cc);
 #pragma unroll
       for (int mu = 0; mu < NMU; ++mu) {
-        const R cc = R(c[mu * nq + k]);
-        A[mu] = fmadd(cc, t2, A[mu]);
-        if (DERIV) Bd[mu] = fmadd(cc, d2, Bd[mu]);
+        A[mu] = fmadd(R(cc[mu]), t2, A[mu]);
+        if (DERIV) Bd[mu] = fmadd(R(cc[mu]), d2, Bd[mu]);
       }
       if (WANT_Q) q[k] = t2 * cut2;
       t0 = t1; t1 = t2; d0 = d1; d1 = d2;
@@ -227,6 +279,17 @@ __device__ __forceinline__ void radial(const C* __restrict__ c, int nq, R r, R m
   for (int mu = 0; mu < NMU; ++mu) {
     f[mu] = cut2 * A[mu];
     if (DERIV) df[mu] = fmadd(scale * cut2, Bd[mu], R(-2) * cut * A[mu]);
+  }
+}
+
+// Fills the pair blocks of CoefLayout from the global layout [mu][k][zi][zj]
+// (called by every thread of the block).
+template <class C, int NMU, class SRC>
+__device__ __forceinline__ void fill_coefs(C* dst, const SRC* __restrict__ src, int SS, int nq) {
+  using L = CoefLayout<C, NMU>;
+  for (int t = threadIdx.x; t < NMU * nq * SS; t += blockDim.x) {
+    const int pair = t % SS, mk = t / SS;
+    dst[pair * L::cstride(nq) + L::at(mk / nq, mk % nq)] = C(src[t]);
   }
 }
 
@@ -305,7 +368,7 @@ __device__ __forceinline__ void close_pair_fp64(const EfvArgs& a, const double* 
 // Byte offset of the FP64 reduction area in the kernel's dynamic shared memory.
 template <class R, int NMU, bool DTHETA>
 __host__ __device__ __forceinline__ size_t efv_red_offset(int SS, int nq, int m) {
-  const size_t cstride = (size_t)((NMU * nq) | 1);
+  const size_t cstride = (size_t)CoefLayout<R, NMU>::cstride(nq);
   size_t bytes = sizeof(R) * ((size_t)SS * cstride + m);
   if (DTHETA) bytes += sizeof(R) * ((size_t)SS * NMU * nq + m);
   return (bytes + 15) & ~size_t(15);
@@ -354,9 +417,8 @@ template <class R> struct AccView {
   __device__ __forceinline__ R& operator[](int t) const { return p[t * stride]; }
 };
 
-// Shared-memory view: radial coefficients [zi*S+zj][mu][k] (odd stride: the
-// species-pair blocks fall on distinct banks), xi, and with DTHETA the
-// per-block gradient accumulators.
+// Shared-memory view: radial coefficients (pair blocks of CoefLayout), xi,
+// and with DTHETA the per-block gradient accumulators.
 template <class R, int NMU, bool DTHETA>
 struct EfvShared {
   R* c;
@@ -374,7 +436,7 @@ struct EfvShared {
     SS = S * S;
     nq = a.n_q;
     m = a.m;
-    cstride = (NMU * nq) | 1;
+    cstride = CoefLayout<R, NMU>::cstride(nq);
     c = reinterpret_cast<R*>(raw);
     xi = c + SS * cstride;
     dc = xi + m;
@@ -396,10 +458,7 @@ struct EfvShared {
       radial_src = reinterpret_cast<const R*>(a.radial_f);
       xi_src = reinterpret_cast<const R*>(a.xi_f);
     }
-    for (int t = threadIdx.x; t < NMU * nq * SS; t += blockDim.x) {
-      // global layout [mu][k][zi][zj] -> shared [zi*S+zj][mu][k]
-      c[(t % SS) * cstride + t / SS] = radial_src[t];
-    }
+    fill_coefs<R, NMU>(c, radial_src, SS, nq);
     for (int t = threadIdx.x; t < m; t += blockDim.x) xi[t] = xi_src[t];
     rcut = R(a.r_cut);
     rmin = R(a.r_min);
@@ -418,7 +477,47 @@ struct EfvShared {
 // First neighbour sweep: M[c] += f_mu(r_ij) rhat^K for the components of
 // group G (G < 0: all components; G >= 0: the level's component group G).
 // CLOSE64 (mixed path only): pairs closer than R_min take close_pair_fp64.
-template <class LV, class R, bool DTHETA, int G, bool CLOSE64 = false>
+// Geometry and radial functions of one pair for the first sweep: f_mu(r) and
+// the unit vector u = r_ij / r.
+template <class LV, class R, bool DTHETA, int NQ>
+__device__ __forceinline__ void pair_radial(const EfvArgs& a, const EfvShared<R, LV::NMU, DTHETA>& sm,
+                                            const PairGeom<R>& geom, int zi, const typename PairGeom<R>::Load& lj,
+                                            int32_t img, R* f, R& ux, R& uy, R& uz) {
+  R dx, dy, dz;
+  geom.vec(a, lj, img, dx, dy, dz);
+  const R r2 = fmadd(dz, dz, fmadd(dy, dy, dx * dx));
+  const R rinv = rsqrt_r(r2);
+  const R r = r2 * rinv;
+  radial<R, LV::NMU, false, false, NQ>(sm.c + (zi * sm.S + lj.species) * sm.cstride, sm.nq, r, sm.mid, sm.scale,
+                                       sm.rcut, f, nullptr, nullptr);
+  ux = dx * rinv;
+  uy = dy * rinv;
+  uz = dz * rinv;
+}
+
+// The same for the second sweep: also df_mu/dr, the pair vector, 1/r and,
+// with DTHETA, the basis values Q_k(r).
+template <class LV, class R, bool DTHETA, int NQ>
+struct PairTerms {
+  R f[LV::NMU], df[LV::NMU], q[DTHETA ? kMaxQ : 1];
+  R dx, dy, dz, rinv;
+  int32_t j;
+  int zj;
+  __device__ __forceinline__ void eval(const EfvArgs& a, const EfvShared<R, LV::NMU, DTHETA>& sm,
+                                       const PairGeom<R>& geom, int zi, int32_t j_, int32_t img,
+                                       const typename PairGeom<R>::Load& lj) {
+    j = j_;
+    zj = lj.species;
+    geom.vec(a, lj, img, dx, dy, dz);
+    const R r2 = fmadd(dz, dz, fmadd(dy, dy, dx * dx));
+    rinv = rsqrt_r(r2);
+    const R r = r2 * rinv;
+    radial<R, LV::NMU, true, DTHETA, NQ>(sm.c + (zi * sm.S + zj) * sm.cstride, sm.nq, r, sm.mid, sm.scale,
+                                         sm.rcut, f, df, q);
+  }
+};
+
+template <class LV, class R, bool DTHETA, int G, bool CLOSE64 = false, int NQ = 0>
 __device__ __forceinline__ void moment_sweep(const EfvArgs& a, const EfvShared<R, LV::NMU, DTHETA>& sm,
                                              const PairGeom<R>& geom, const double* cell64, int zi, int64_t beg,
                                              int64_t end, R* M) {
@@ -427,6 +526,27 @@ __device__ __forceinline__ void moment_sweep(const EfvArgs& a, const EfvShared<R
   int32_t j, img;
   typename PairGeom<R>::Load lj;
   ps.start(a, geom, beg, end);
+  if constexpr (!CLOSE64) {
+    // software-pipelined: the geometry and radial functions of the next pair
+    // (one basic block with this pair's moment terms, so that the scheduler
+    // overlaps the latency chain of the one with the independent FMAs of
+    // the other)
+    if (beg >= end) return;
+    R f[NMU], ux, uy, uz;
+    ps.step(a, geom, j, img, lj);
+    pair_radial<LV, R, DTHETA, NQ>(a, sm, geom, zi, lj, img, f, ux, uy, uz);
+    for (int64_t p = beg; p < end; ++p) {
+      R fn[NMU], uxn, uyn, uzn;
+      ps.step(a, geom, j, img, lj);
+      pair_radial<LV, R, DTHETA, NQ>(a, sm, geom, zi, lj, img, fn, uxn, uyn, uzn);
+      if constexpr (G < 0) LV::template moments<R>(M, f, ux, uy, uz);
+      else LV::template moments_group<G, R>(M, f, ux, uy, uz);
+#pragma unroll
+      for (int mu = 0; mu < NMU; ++mu) f[mu] = fn[mu];
+      ux = uxn; uy = uyn; uz = uzn;
+    }
+    return;
+  }
   while (ps.next(a, geom, j, img, lj)) {
     R dx, dy, dz;
     geom.vec(a, lj, img, dx, dy, dz);
@@ -439,23 +559,78 @@ __device__ __forceinline__ void moment_sweep(const EfvArgs& a, const EfvShared<R
         close_pair_fp64<NMU, false, false>(a, cell64, geom.ci, j, img, zi, lj.species, dx, dy,
                                            dz, rinv, f, nullptr, nullptr);
       else
-        radial<R, NMU, false, false>(sm.c + (zi * sm.S + lj.species) * sm.cstride, sm.nq, r, sm.mid, sm.scale,
-                                     sm.rcut, f, nullptr, nullptr);
+        radial<R, NMU, false, false, NQ>(sm.c + (zi * sm.S + lj.species) * sm.cstride, sm.nq, r, sm.mid,
+                                         sm.scale, sm.rcut, f, nullptr, nullptr);
     } else {
-      radial<R, NMU, false, false>(sm.c + (zi * sm.S + lj.species) * sm.cstride, sm.nq, r, sm.mid, sm.scale, sm.rcut,
-                                   f, nullptr, nullptr);
+      radial<R, NMU, false, false, NQ>(sm.c + (zi * sm.S + lj.species) * sm.cstride, sm.nq, r, sm.mid, sm.scale,
+                                       sm.rcut, f, nullptr, nullptr);
     }
     if constexpr (G < 0) LV::template moments<R>(M, f, dx * rinv, dy * rinv, dz * rinv);
     else LV::template moments_group<G, R>(M, f, dx * rinv, dy * rinv, dz * rinv);
   }
 }
 
+// One pair of the second sweep: g = dE_i/dr_ij from D, the force and virial
+// terms and, with DTHETA, the dE/dc terms Q_k(r) S_mu.
+template <class LV, class R, bool DTHETA, int G, int NQ>
+__device__ __forceinline__ void adjoint_pair(const EfvArgs& a, const EfvShared<R, LV::NMU, DTHETA>& sm, int zi,
+                                             int32_t j, int zj, R dx, R dy, R dz, R rinv, const R* f, const R* df,
+                                             const R* q, const R* D, R& fx, R& fy, R& fz, R* w, AccView<R> acc,
+                                             bool own_acc) {
+  constexpr int NMU = LV::NMU;
+  R gx, gy, gz, Smu[NMU];
+  if constexpr (G < 0)
+    LV::template pair_adjoint<R>(D, f, df, dx * rinv, dy * rinv, dz * rinv, rinv, gx, gy, gz, Smu);
+  else
+    LV::template pair_adjoint_group<G, R>(D, f, df, dx * rinv, dy * rinv, dz * rinv, rinv, gx, gy, gz, Smu);
+  fx += gx; fy += gy; fz += gz;
+  scatter_force(a, j, -gx, -gy, -gz);
+  w[0] = fmadd(-gx, dx, w[0]);
+  w[1] = fmadd(-gy, dy, w[1]);
+  w[2] = fmadd(-gz, dz, w[2]);
+  w[3] = fmadd(R(-0.5), fmadd(gx, dy, gy * dx), w[3]);
+  w[4] = fmadd(R(-0.5), fmadd(gx, dz, gz * dx), w[4]);
+  w[5] = fmadd(R(-0.5), fmadd(gy, dz, gz * dy), w[5]);
+  if (DTHETA) {
+    int mu_lo = 0, mu_hi = NMU;
+    if constexpr (G >= 0) {
+      mu_lo = LV::GROUP_MU_LO[G];
+      mu_hi = LV::GROUP_MU_HI[G];
+    }
+    const int nq = NQ > 0 ? NQ : sm.nq;
+    if (own_acc) {
+      const int base = zj * NMU * nq;
+#pragma unroll
+      for (int mu = 0; mu < NMU; ++mu) {
+        if (mu < mu_lo || mu >= mu_hi) continue;
+#pragma unroll
+        for (int kk = 0; kk < kMaxQ; ++kk)
+          if (kk < nq) {
+            R& d = acc[base + mu * nq + kk];
+            d = fmadd(q[kk], Smu[mu], d);
+          }
+      }
+    } else {
+      R* dst = sm.dc + (zi * sm.S + zj) * NMU * nq;
+#pragma unroll
+      for (int mu = 0; mu < NMU; ++mu) {
+        if (mu < mu_lo || mu >= mu_hi) continue;
+#pragma unroll
+        for (int kk = 0; kk < kMaxQ; ++kk)
+          if (kk < nq) atomicAdd(dst + mu * nq + kk, q[kk] * Smu[mu]);
+      }
+    }
+  }
+
+}
+
 // Second neighbour sweep for the components of group G (G < 0: all): per pair
 // g_ij = dE_i/dr_ij from D (the group's share), F_i += g, F_j -= g,
 // W -= sym(g (x) r_ij) and, with DTHETA, the group's radial functions'
 // dE/dc terms Q_k(r) S_mu into acc (own_acc) or the shared accumulators.
-// CLOSE64 as in moment_sweep.
-template <class LV, class R, bool DTHETA, int G, bool CLOSE64 = false>
+// CLOSE64 as in moment_sweep; without it the sweep is software-pipelined
+// like moment_sweep.
+template <class LV, class R, bool DTHETA, int G, bool CLOSE64 = false, int NQ = 0>
 __device__ __forceinline__ void adjoint_sweep(const EfvArgs& a, const EfvShared<R, LV::NMU, DTHETA>& sm,
                                               const PairGeom<R>& geom, const double* cell64, int zi, int64_t beg,
                                               int64_t end,
@@ -466,6 +641,21 @@ __device__ __forceinline__ void adjoint_sweep(const EfvArgs& a, const EfvShared<
   int32_t j, img;
   typename PairGeom<R>::Load lj;
   ps.start(a, geom, beg, end);
+  if constexpr (!CLOSE64) {
+    if (beg >= end) return;
+    PairTerms<LV, R, DTHETA, NQ> cur;
+    ps.step(a, geom, j, img, lj);
+    cur.eval(a, sm, geom, zi, j, img, lj);
+    for (int64_t p = beg; p < end; ++p) {
+      PairTerms<LV, R, DTHETA, NQ> nxt;
+      ps.step(a, geom, j, img, lj);
+      nxt.eval(a, sm, geom, zi, j, img, lj);
+      adjoint_pair<LV, R, DTHETA, G, NQ>(a, sm, zi, cur.j, cur.zj, cur.dx, cur.dy, cur.dz, cur.rinv, cur.f, cur.df,
+                                          cur.q, D, fx, fy, fz, w, acc, own_acc);
+      cur = nxt;
+    }
+    return;
+  }
   while (ps.next(a, geom, j, img, lj)) {
     const int zj = lj.species;
     R dx, dy, dz;
@@ -474,59 +664,17 @@ __device__ __forceinline__ void adjoint_sweep(const EfvArgs& a, const EfvShared<
     R rinv = rsqrt_r(r2);
     const R r = r2 * rinv;
     R f[NMU], df[NMU], q[DTHETA ? kMaxQ : 1];
-    if constexpr (CLOSE64 && std::is_same<R, float>::value) {
+    if constexpr (std::is_same<R, float>::value) {
       if (r < sm.rmin)
-        close_pair_fp64<NMU, true, DTHETA>(a, cell64, geom.ci, j, img, zi, zj, dx, dy, dz, rinv,
-                                           f, df, q);
+        close_pair_fp64<NMU, true, DTHETA>(a, cell64, geom.ci, j, img, zi, zj, dx, dy, dz, rinv, f, df, q);
       else
-        radial<R, NMU, true, DTHETA>(sm.c + (zi * sm.S + zj) * sm.cstride, sm.nq, r, sm.mid, sm.scale, sm.rcut, f, df,
-                                     q);
+        radial<R, NMU, true, DTHETA, NQ>(sm.c + (zi * sm.S + zj) * sm.cstride, sm.nq, r, sm.mid, sm.scale, sm.rcut,
+                                         f, df, q);
     } else {
-      radial<R, NMU, true, DTHETA>(sm.c + (zi * sm.S + zj) * sm.cstride, sm.nq, r, sm.mid, sm.scale, sm.rcut, f, df,
-                                   q);
+      radial<R, NMU, true, DTHETA, NQ>(sm.c + (zi * sm.S + zj) * sm.cstride, sm.nq, r, sm.mid, sm.scale, sm.rcut, f,
+                                       df, q);
     }
-    R gx, gy, gz, Smu[NMU];
-    if constexpr (G < 0)
-      LV::template pair_adjoint<R>(D, f, df, dx * rinv, dy * rinv, dz * rinv, rinv, gx, gy, gz, Smu);
-    else
-      LV::template pair_adjoint_group<G, R>(D, f, df, dx * rinv, dy * rinv, dz * rinv, rinv, gx, gy, gz, Smu);
-    fx += gx; fy += gy; fz += gz;
-    scatter_force(a, j, -gx, -gy, -gz);
-    w[0] = fmadd(-gx, dx, w[0]);
-    w[1] = fmadd(-gy, dy, w[1]);
-    w[2] = fmadd(-gz, dz, w[2]);
-    w[3] = fmadd(R(-0.5), fmadd(gx, dy, gy * dx), w[3]);
-    w[4] = fmadd(R(-0.5), fmadd(gx, dz, gz * dx), w[4]);
-    w[5] = fmadd(R(-0.5), fmadd(gy, dz, gz * dy), w[5]);
-    if (DTHETA) {
-      int mu_lo = 0, mu_hi = NMU;
-      if constexpr (G >= 0) {
-        mu_lo = LV::GROUP_MU_LO[G];
-        mu_hi = LV::GROUP_MU_HI[G];
-      }
-      if (own_acc) {
-        const int base = zj * NMU * sm.nq;
-#pragma unroll
-        for (int mu = 0; mu < NMU; ++mu) {
-          if (mu < mu_lo || mu >= mu_hi) continue;
-#pragma unroll
-          for (int kk = 0; kk < kMaxQ; ++kk)
-            if (kk < sm.nq) {
-              R& d = acc[base + mu * sm.nq + kk];
-              d = fmadd(q[kk], Smu[mu], d);
-            }
-        }
-      } else {
-        R* dst = sm.dc + (zi * sm.S + zj) * NMU * sm.nq;
-#pragma unroll
-        for (int mu = 0; mu < NMU; ++mu) {
-          if (mu < mu_lo || mu >= mu_hi) continue;
-#pragma unroll
-          for (int kk = 0; kk < kMaxQ; ++kk)
-            if (kk < sm.nq) atomicAdd(dst + mu * sm.nq + kk, q[kk] * Smu[mu]);
-        }
-      }
-    }
+    adjoint_pair<LV, R, DTHETA, G, NQ>(a, sm, zi, j, zj, dx, dy, dz, rinv, f, df, q, D, fx, fy, fz, w, acc, own_acc);
   }
 }
 
@@ -544,7 +692,7 @@ __device__ __forceinline__ void adjoint_sweep(const EfvArgs& a, const EfvShared<
 // and 20: 201 and 295 components) sweep the neighbours once per group, so
 // that a group's moments, then its adjoints, stay in registers; the full
 // vectors meet the interpreter once per atom.
-template <class LV, class R, bool DTHETA, bool PHASE_SYNC = false>
+template <class LV, class R, bool DTHETA, bool PHASE_SYNC = false, int NQ = 0>
 __device__ __forceinline__ void efv_atom(const EfvArgs& a, const EfvShared<R, LV::NMU, DTHETA>& sm, int64_t i,
                                          bool active, const R* cell, const double* cell64, double& e_i, R* w) {
   constexpr int NMU = LV::NMU;
@@ -557,7 +705,7 @@ __device__ __forceinline__ void efv_atom(const EfvArgs& a, const EfvShared<R, LV
 #pragma unroll
   for (int c = 0; c < LV::NCOMP; ++c) M[c] = R(0);
   if constexpr (LV::NGROUPS == 1) {
-    moment_sweep<LV, R, DTHETA, -1>(a, sm, geom, cell64, zi, beg, end, M);
+    moment_sweep<LV, R, DTHETA, -1, false, NQ>(a, sm, geom, cell64, zi, beg, end, M);
   } else {
     {
       R Mg[LV::NCOMP];
@@ -616,7 +764,7 @@ __device__ __forceinline__ void efv_atom(const EfvArgs& a, const EfvShared<R, LV
     for (int t = 0; t < sm.S * NMU * sm.nq; ++t) acc[t] = R(0);
   }
   if constexpr (LV::NGROUPS == 1) {
-    adjoint_sweep<LV, R, DTHETA, -1>(a, sm, geom, cell64, zi, beg, end, D, fx, fy, fz, w, acc, own_acc);
+    adjoint_sweep<LV, R, DTHETA, -1, false, NQ>(a, sm, geom, cell64, zi, beg, end, D, fx, fy, fz, w, acc, own_acc);
   } else {
     {
       R Dg[LV::NCOMP];
@@ -685,7 +833,7 @@ __device__ __forceinline__ void efv_block_flush(const EfvShared<R, LV::NMU, DTHE
   }
 }
 
-template <class LV, class R, bool DTHETA>
+template <class LV, class R, bool DTHETA, int NQ = 0>
 __global__ void __launch_bounds__(kEfvFusedThreads) efv_kernel(const EfvArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   EfvShared<R, LV::NMU, DTHETA> sm;
@@ -699,7 +847,7 @@ __global__ void __launch_bounds__(kEfvFusedThreads) efv_kernel(const EfvArgs a) 
   // the block's warps meet between the neighbour sweeps and the contraction,
   // so that they run the same code at the same time (instruction cache); a
   // warp without atoms runs the phases on zero pairs
-  efv_atom<LV, R, DTHETA, true>(a, sm, active ? i : a.atom_begin, active, cell_of<R>(a), a.cell, e_i, w);
+  efv_atom<LV, R, DTHETA, true, NQ>(a, sm, active ? i : a.atom_begin, active, cell_of<R>(a), a.cell, e_i, w);
   efv_block_flush<LV, R, DTHETA>(sm, e_i, w, a.e_total, a.virial, a.dtheta);
 }
 
@@ -835,6 +983,8 @@ __global__ void __launch_bounds__(kEfvThreads) split_adjoint_kernel(const EfvArg
   efv_block_flush<LV, R, DTHETA>(sm, 0.0, w, a.e_total, a.virial, a.dtheta, kFlushEW | kFlushDc);
 }
 
+constexpr int kFixedQ = 8;
+
 template <class K>
 int set_smem(K kern, size_t bytes) {
   if (bytes > 48 * 1024) {
@@ -880,6 +1030,11 @@ int efv_launch_typed(const EfvArgs& a, cudaStream_t stream) {
   const size_t bytes = ((efv_smem_bytes<R, LV::NMU, DTHETA>(SS, a.n_q, a.m) + 15) & ~size_t(15)) +
                        efv_acc_bytes<R, LV::NMU, DTHETA>(a.n_species, a.n_q, kEfvFusedThreads);
   auto kern = efv_kernel<LV, R, DTHETA>;
+  // the mixed path of the single-group levels with the common radial basis
+  // size n_q = 8 runs with n_q fixed at compile time
+  if constexpr (std::is_same<R, float>::value && LV::NGROUPS == 1) {
+    if (a.n_q == kFixedQ) kern = efv_kernel<LV, R, DTHETA, kFixedQ>;
+  }
   if (bytes > 48 * 1024) {
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
     if (e != cudaSuccess) {

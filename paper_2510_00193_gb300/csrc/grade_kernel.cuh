@@ -25,10 +25,10 @@ __global__ void __launch_bounds__(kRowsThreads) basis_rows_kernel(const EfvArgs 
   const int S = a.n_species;
   const int SS = S * S;
   const int nq = a.n_q;
-  const int cstride = (NMU * nq) | 1;
+  const int cstride = CoefLayout<R, NMU>::cstride(nq);
   R* s_c = reinterpret_cast<R*>(smem_raw);
   R* s_xi = s_c + SS * cstride;
-  for (int t = threadIdx.x; t < NMU * nq * SS; t += blockDim.x) s_c[(t % SS) * cstride + t / SS] = a.radial_d[t];
+  fill_coefs<R, NMU>(s_c, a.radial_d, SS, nq);
   for (int t = threadIdx.x; t < a.m; t += blockDim.x) s_xi[t] = a.xi_d[t];
   __syncthreads();
 
@@ -84,7 +84,7 @@ int basis_rows_launch(const EfvArgs& a, const int32_t* list, int64_t n_rows, dou
                       cudaStream_t stream) {
   if (n_rows <= 0) return MTP_OK;
   const int SS = a.n_species * a.n_species;
-  const size_t bytes = sizeof(double) * ((size_t)SS * ((LV::NMU * a.n_q) | 1) + a.m);
+  const size_t bytes = sizeof(double) * ((size_t)SS * CoefLayout<double, LV::NMU>::cstride(a.n_q) + a.m);
   auto kern = basis_rows_kernel<LV>;
   if (bytes > 48 * 1024) {
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);

@@ -33,8 +33,8 @@
 // m <= 115 terms and with the int64 truncation of G_8: below 2^-47.8.  Hence
 // |gamma - gamma_exact| <= 2^(e_i + F - 47) + 2^-52 gamma with F = max_k f_k.
 // Rows whose grade lies within max(0.05 tau, bound) of a threshold are
-// re-checked in FP64 (the band of 5% around the thresholds is the one the
-// task specifies for re-checks).
+// re-checked in FP64: a fixed band of 5% around each threshold, widened to
+// the bound where that is larger.
 //
 // Kernel layout (tc_grade_kernel): one CTA per SM, persistent over 128-row
 // tiles, one column half (64 of the padded 128 columns) per CTA.  Shared
