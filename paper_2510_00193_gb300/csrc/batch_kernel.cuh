@@ -26,7 +26,7 @@ struct BatchArgs {
   int64_t n_params;
 };
 
-template <class LV, class R, bool DTHETA>
+template <class LV, class R, bool DTHETA, int NQ = 0>
 __global__ void __launch_bounds__(256) batch_kernel(const BatchArgs b) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ int s_item;
@@ -49,7 +49,8 @@ __global__ void __launch_bounds__(256) batch_kernel(const BatchArgs b) {
     R w[6] = {R(0), R(0), R(0), R(0), R(0), R(0)};
     const bool active = (int)threadIdx.x < count;
     if (__any_sync(0xffffffffu, active))   // warp-uniform: whole warps without atoms skip the work
-      efv_atom<LV, R, DTHETA>(a, sm, active ? first + threadIdx.x : first, active, s_cell, nullptr, e_i, w);
+      efv_atom<LV, R, DTHETA, false, NQ>(a, sm, active ? first + threadIdx.x : first, active, s_cell, nullptr, e_i,
+                                         w);
     efv_block_flush<LV, R, DTHETA>(sm, e_i, w, b.e_cfg + cfg, b.virial_cfg + (int64_t)cfg * 6,
                                    DTHETA ? b.dtheta_cfg + (int64_t)cfg * b.n_params : nullptr);
     __syncthreads();
@@ -62,6 +63,9 @@ int batch_launch_typed(const BatchArgs& b, int threads, cudaStream_t stream) {
   const size_t bytes = ((efv_smem_bytes<R, LV::NMU, DTHETA>(SS, b.base.n_q, b.base.m) + 15) & ~size_t(15)) +
                        efv_acc_bytes<R, LV::NMU, DTHETA>(b.base.n_species, b.base.n_q, threads);
   auto kern = batch_kernel<LV, R, DTHETA>;
+  if constexpr (std::is_same<R, float>::value && LV::NGROUPS == 1) {
+    if (b.base.n_q == kFixedQ) kern = batch_kernel<LV, R, DTHETA, kFixedQ>;
+  }
   if (bytes > 48 * 1024) {
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
     if (e != cudaSuccess) {

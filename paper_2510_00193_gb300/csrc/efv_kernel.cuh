@@ -477,6 +477,10 @@ struct EfvShared {
 // First neighbour sweep: M[c] += f_mu(r_ij) rhat^K for the components of
 // group G (G < 0: all components; G >= 0: the level's component group G).
 // CLOSE64 (mixed path only): pairs closer than R_min take close_pair_fp64.
+// Which sweeps are software-pipelined when DTHETA is set (without it both are).
+constexpr bool kPipeMomentsDtheta = true;
+constexpr bool kPipeAdjointDtheta = false;
+
 // Geometry and radial functions of one pair for the first sweep: f_mu(r) and
 // the unit vector u = r_ij / r.
 template <class LV, class R, bool DTHETA, int NQ>
@@ -526,7 +530,7 @@ __device__ __forceinline__ void moment_sweep(const EfvArgs& a, const EfvShared<R
   int32_t j, img;
   typename PairGeom<R>::Load lj;
   ps.start(a, geom, beg, end);
-  if constexpr (!CLOSE64) {
+  if constexpr (!CLOSE64 && (kPipeMomentsDtheta || !DTHETA)) {
     // software-pipelined: the geometry and radial functions of the next pair
     // (one basic block with this pair's moment terms, so that the scheduler
     // overlaps the latency chain of the one with the independent FMAs of
@@ -628,8 +632,9 @@ __device__ __forceinline__ void adjoint_pair(const EfvArgs& a, const EfvShared<R
 // g_ij = dE_i/dr_ij from D (the group's share), F_i += g, F_j -= g,
 // W -= sym(g (x) r_ij) and, with DTHETA, the group's radial functions'
 // dE/dc terms Q_k(r) S_mu into acc (own_acc) or the shared accumulators.
-// CLOSE64 as in moment_sweep; without it the sweep is software-pipelined
-// like moment_sweep.
+// CLOSE64 as in moment_sweep; without it and without DTHETA the sweep is
+// software-pipelined like moment_sweep (with DTHETA the next pair's Q_k
+// values would stay live as well, which measured slower).
 template <class LV, class R, bool DTHETA, int G, bool CLOSE64 = false, int NQ = 0>
 __device__ __forceinline__ void adjoint_sweep(const EfvArgs& a, const EfvShared<R, LV::NMU, DTHETA>& sm,
                                               const PairGeom<R>& geom, const double* cell64, int zi, int64_t beg,
@@ -641,7 +646,7 @@ __device__ __forceinline__ void adjoint_sweep(const EfvArgs& a, const EfvShared<
   int32_t j, img;
   typename PairGeom<R>::Load lj;
   ps.start(a, geom, beg, end);
-  if constexpr (!CLOSE64) {
+  if constexpr (!CLOSE64 && (kPipeAdjointDtheta || !DTHETA)) {
     if (beg >= end) return;
     PairTerms<LV, R, DTHETA, NQ> cur;
     ps.step(a, geom, j, img, lj);
