@@ -1012,11 +1012,14 @@ int efv_split_launch(const EfvArgs& a, cudaStream_t stream) {
   const size_t b1 = ((efv_smem_bytes<R, LV::NMU, DTHETA>(SS, a.n_q, a.m) + 15) & ~size_t(15)) +
                     efv_acc_bytes<R, LV::NMU, DTHETA>(a.n_species, a.n_q, kEfvThreads);
   int rc;
+  // the contraction kernel has no dE/dc accumulators: without them its blocks
+  // stay small, so that many warps hide the interpreter's local-memory traffic
+  const size_t bc = efv_smem_bytes<R, LV::NMU, DTHETA>(SS, a.n_q, a.m);
   if ((rc = set_smem(split_moments_kernel<LV, R>, b0)) != MTP_OK) return rc;
-  if ((rc = set_smem(split_contract_kernel<LV, R, DTHETA>, b1)) != MTP_OK) return rc;
+  if ((rc = set_smem(split_contract_kernel<LV, R, DTHETA>, bc)) != MTP_OK) return rc;
   if ((rc = set_smem(split_adjoint_kernel<LV, R, DTHETA>, b1)) != MTP_OK) return rc;
   split_moments_kernel<LV, R><<<grid, kEfvThreads, b0, stream>>>(a);
-  split_contract_kernel<LV, R, DTHETA><<<grid, kEfvThreads, b1, stream>>>(a);
+  split_contract_kernel<LV, R, DTHETA><<<grid, kEfvThreads, bc, stream>>>(a);
   split_adjoint_kernel<LV, R, DTHETA><<<grid, kEfvThreads, b1, stream>>>(a);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) {

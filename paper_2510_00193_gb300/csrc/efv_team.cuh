@@ -27,10 +27,11 @@ __host__ __device__ __forceinline__ size_t team_buf_bytes(int ncomp) {
   return sizeof(R) * (size_t)kTeamWarps * (size_t)ncomp * 33;
 }
 
-template <class LV, class R, bool DTHETA>
+template <class LV, class R, bool DTHETA, int NQ = 0>
 __global__ void __launch_bounds__(kEfvThreads) efv_team_kernel(const EfvArgs a) {
   static_assert(LV::NGROUPS == 1, "warp-per-atom kernel: levels with one component group");
   constexpr int NMU = LV::NMU;
+  const int nq = NQ > 0 ? NQ : a.n_q;
   constexpr int C = LV::NCOMP;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   EfvShared<R, NMU, DTHETA> sm;
@@ -65,8 +66,8 @@ __global__ void __launch_bounds__(kEfvThreads) efv_team_kernel(const EfvArgs a) 
       const R rinv = rsqrt_r(r2);
       const R r = r2 * rinv;
       R f[NMU];
-      radial<R, NMU, false, false>(cz + lj.species * sm.cstride, sm.nq, r, sm.mid, sm.scale, sm.rcut, f, nullptr,
-                                   nullptr);
+      radial<R, NMU, false, false, NQ>(cz + lj.species * sm.cstride, sm.nq, r, sm.mid, sm.scale, sm.rcut, f,
+                                       nullptr, nullptr);
       LV::template moments<R>(M, f, dx * rinv, dy * rinv, dz * rinv);
     }
     // reduce across the warp through the transpose buffer
@@ -100,7 +101,7 @@ __global__ void __launch_bounds__(kEfvThreads) efv_team_kernel(const EfvArgs a) 
     const bool own_acc = DTHETA && sm.S <= kAccS;
     R acc[DTHETA ? kAccS * NMU * kMaxQ : 1];
     if (own_acc) {
-      for (int t = 0; t < sm.S * NMU * sm.nq; ++t) acc[t] = R(0);
+      for (int t = 0; t < sm.S * NMU * nq; ++t) acc[t] = R(0);
     }
     for (int64_t k = beg + lane; k < end; k += 32) {
       const int32_t j = __ldg(a.nbr_j + k), img = __ldg(a.nbr_img + k);
@@ -112,7 +113,7 @@ __global__ void __launch_bounds__(kEfvThreads) efv_team_kernel(const EfvArgs a) 
       const R rinv = rsqrt_r(r2);
       const R r = r2 * rinv;
       R f[NMU], df[NMU], q[DTHETA ? kMaxQ : 1];
-      radial<R, NMU, true, DTHETA>(cz + zj * sm.cstride, sm.nq, r, sm.mid, sm.scale, sm.rcut, f, df, q);
+      radial<R, NMU, true, DTHETA, NQ>(cz + zj * sm.cstride, sm.nq, r, sm.mid, sm.scale, sm.rcut, f, df, q);
       R gx, gy, gz, Smu[NMU];
       LV::template pair_adjoint<R>(D, f, df, dx * rinv, dy * rinv, dz * rinv, rinv, gx, gy, gz, Smu);
       fx += gx;
@@ -127,19 +128,19 @@ __global__ void __launch_bounds__(kEfvThreads) efv_team_kernel(const EfvArgs a) 
       w[5] = fmadd(R(-0.5), fmadd(gy, dz, gz * dy), w[5]);
       if (DTHETA) {
         if (own_acc) {
-          R* dst = acc + zj * NMU * sm.nq;
+          R* dst = acc + zj * NMU * nq;
 #pragma unroll
           for (int mu = 0; mu < NMU; ++mu)
 #pragma unroll
             for (int kk = 0; kk < kMaxQ; ++kk)
-              if (kk < sm.nq) dst[mu * sm.nq + kk] = fmadd(q[kk], Smu[mu], dst[mu * sm.nq + kk]);
+              if (kk < nq) dst[mu * nq + kk] = fmadd(q[kk], Smu[mu], dst[mu * nq + kk]);
         } else {
-          R* dst = sm.dc + (zi * sm.S + zj) * NMU * sm.nq;
+          R* dst = sm.dc + (zi * sm.S + zj) * NMU * nq;
 #pragma unroll
           for (int mu = 0; mu < NMU; ++mu)
 #pragma unroll
             for (int kk = 0; kk < kMaxQ; ++kk)
-              if (kk < sm.nq) atomicAdd(dst + mu * sm.nq + kk, q[kk] * Smu[mu]);
+              if (kk < nq) atomicAdd(dst + mu * nq + kk, q[kk] * Smu[mu]);
         }
       }
     }
@@ -382,6 +383,9 @@ int efv_team_launch_typed(const EfvArgs& a, cudaStream_t stream) {
     const size_t bytes = ((efv_smem_bytes<R, LV::NMU, DTHETA>(SS, a.n_q, a.m) + 15) & ~size_t(15)) +
                          team_buf_bytes<R>(LV::NCOMP);
     auto kern = efv_team_kernel<LV, R, DTHETA>;
+    if constexpr (std::is_same<R, float>::value) {
+      if (a.n_q == kFixedQ) kern = efv_team_kernel<LV, R, DTHETA, kFixedQ>;
+    }
     int rc = set_smem(kern, bytes);
     if (rc != MTP_OK) return rc;
     const int64_t n = a.atom_end - a.atom_begin;
