@@ -143,7 +143,12 @@ def test_batch_replays_under_a_cuda_graph(P, small_batch):
     g.replay()
     torch.cuda.synchronize()
     assert torch.allclose(out["e_cfg"], ref["e_cfg"], rtol=0, atol=1e-9)
-    assert torch.allclose(out["forces"], ref["forces"], rtol=0, atol=1e-5)
+    # forces: FP32 atomics from every pair in an order that differs between
+    # runs; a force is a sum of ~50 pair terms, so replays agree to a few units
+    # of 2^-24 times the largest force, not to an absolute 1e-5 (the random
+    # gases have forces of tens of eV/A at their closest contacts)
+    fscale = max(1.0, ref["forces"].abs().max().item())
+    assert (out["forces"] - ref["forces"]).abs().max().item() <= 2.0 ** -17 * fscale
     # FP32 shared-memory atomics: the order of the additions differs between runs
     scale = ref["dtheta"].abs().max().item()
     assert (out["dtheta"] - ref["dtheta"]).abs().max().item() <= 1e-5 * scale
