@@ -36,6 +36,12 @@ from collections import defaultdict
 
 import numpy as np
 
+# levels from which the contraction runs as an interpreted program
+INTERPRET_FROM_LEVEL = 18
+# levels whose neighbour sweeps work on the components with a z-exponent of at
+# most 1 (the others follow from |rhat| = 1 in the contraction)
+SPHERE_MAX_LEVEL = 16
+
 # ---------------------------------------------------------------------------
 # graphs and basis functions
 # ---------------------------------------------------------------------------
@@ -391,6 +397,20 @@ class Level:
         self.nu_max = [max([n for m, n in self.layout if m == mu], default=-1) for mu in range(self.nmu)]
         self.comps = [(mu, K) for mu, nu in self.layout for K in multi_indices(nu)]
         self.comp_index = {c: i for i, c in enumerate(self.comps)}
+        # components the neighbour sweeps accumulate.  Because rhat is a unit
+        # vector, u^(a,b,c) = u^(a,b,c-2) - u^(a+2,b,c-2) - u^(a,b+2,c-2) for
+        # c >= 2, so with every degree 0..nu_max present for each mu the
+        # components with a z-exponent of at most 1 determine all others
+        # (SPHERE_MAX_LEVEL: levels that use this; above it all are swept)
+        self.expand = {}
+        if level <= SPHERE_MAX_LEVEL:
+            for c, (mu, K) in enumerate(self.comps):
+                a, b, z = K
+                if z >= 2:
+                    src = [(mu, (a, b, z - 2)), (mu, (a + 2, b, z - 2)), (mu, (a, b + 2, z - 2))]
+                    assert all(t in self.comp_index for t in src), (level, mu, K)
+                    self.expand[c] = tuple(self.comp_index[t] for t in src)
+        self.swept = [c for c in range(len(self.comps)) if c not in self.expand]
         self.dag = Dag()
         self.roots = [self.dag.graph(g) for g in self.graphs]
         # levels with an interpreted contraction sweep the neighbours once per
@@ -507,9 +527,12 @@ def emit_moments(lv: Level, subset=None, fname="moments"):
     L.append(ind + "const R u000 = R(1);")
     by_k = defaultdict(list)
     for c, (mu, K) in enumerate(lv.comps):
-        if subset is None or c in subset:
+        if (subset is None or c in subset) and c not in lv.expand:
             by_k[K].append((c, mu))
+    need = _closure(by_k)
     for K in _monomial_order(max(sum(K) for K in by_k)):
+        if sum(K) > 0 and K not in need:
+            continue
         if sum(K) > 0:
             src, co = _monomial_source(K)
             L.append(ind + "const R %s = %s * %s;" % (_mono_name(K), _mono_name(src), co))
@@ -550,8 +573,8 @@ def emit_pair_adjoint(lv: Level, subset=None, fname="pair_adjoint"):
     L.append("  __device__ __forceinline__ static void %s(const R* __restrict__ D, const R* __restrict__ f, "
              "const R* __restrict__ df, R ux, R uy, R uz, R rinv, R& gx, R& gy, R& gz, R* __restrict__ S) {" % fname)
     L.append(ind + "const R u000 = R(1);")
-    comp = {key: c for key, c in lv.comp_index.items() if subset is None or c in subset}
-    comps = [key for c, key in enumerate(lv.comps) if subset is None or c in subset]
+    comp = {key: c for key, c in lv.comp_index.items() if (subset is None or c in subset) and c not in lv.expand}
+    comps = [key for c, key in enumerate(lv.comps) if (subset is None or c in subset) and c not in lv.expand]
     terms = defaultdict(int)     # accumulator name -> number of terms so far
     parts = defaultdict(list)    # accumulator name -> partial-sum names declared
 
@@ -606,7 +629,14 @@ def emit_pair_adjoint(lv: Level, subset=None, fname="pair_adjoint"):
                 elif deg > 1:
                     L.append(ind + "T%d = fmadd(R(%d), %s, T%d);" % (mu, deg, v, mu))
 
-    order = _monomial_order(maxnu)
+    used = set()
+    for mu, K in comps:
+        used.add(K)
+        for d in range(3):
+            if K[d] > 0:
+                used.add(tuple(K[t] - (t == d) for t in range(3)))
+    need = _closure(used)
+    order = [J for J in _monomial_order(maxnu) if sum(J) == 0 or J in need]
     for idx, J in enumerate(order):
         if sum(J) > 0:
             src, co = _monomial_source(J)
@@ -666,13 +696,21 @@ def emit_contract(lv: Level):
     L.append("  __device__ __forceinline__ static R contract(MV M, "
              "const typename ScalarOf<R>::T* __restrict__ xi, R* __restrict__ D, BV B) {")
     L.append(ind + "(void)B;")
-    # forward
+    # forward.  Components with a z-exponent >= 2 (when the sweeps leave them
+    # out) are formed from the swept ones first, in increasing z-exponent.
+    for c in sorted(lv.expand, key=lambda t: (lv.comps[t][1][2], t)):
+        s0, s1, s2 = (("M[%d]" % t) if t not in lv.expand else ("mx%d" % t) for t in lv.expand[c])
+        L.append(ind + "const R mx%d = (%s - %s) - %s;" % (c, s0, s1, s2))
+
+    def mref(c):
+        return ("mx%d" % c) if c in lv.expand else ("M[%d]" % c)
+
     def comp_ref(n, K):
         key, rank = dag.nodes[n]
         if key[0] == "M":
             _, mu, nu, off = key
             full = (off[0] + K[0], off[1] + K[1], off[2] + K[2])
-            return "M[%d]" % lv.comp_index[(mu, full)]
+            return mref(lv.comp_index[(mu, full)])
         return "v%d_%d" % (n, multi_indices(rank).index(K))
 
     wname = {}
@@ -778,15 +816,34 @@ def emit_contract(lv: Level):
             emit_dot(L, ind, nm, lst)
             bidx = j
             adj[(b, bidx)].append(nm if w == 1 else "R(%d) * %s" % (w, nm))
+    # adjoints of the formed components go to the swept ones they came from
+    # (reverse of the expansion, in decreasing z-exponent)
+    dneg = defaultdict(list)
+    for c in sorted(lv.expand, key=lambda t: (-lv.comps[t][1][2], -t)):
+        if not dcontrib.get(c) and not dneg.get(c):
+            continue
+        nm = "dx%d" % c
+        pos = tree_sum(dcontrib.get(c, [])) if dcontrib.get(c) else "R(0)"
+        L.append(ind + "const R %s = %s;" % (nm, pos if not dneg.get(c) else "%s - %s" % (pos, tree_sum(dneg[c]))))
+        s0, s1, s2 = lv.expand[c]
+        dcontrib[s0].append(nm)
+        dneg[s1].append(nm)
+        dneg[s2].append(nm)
     for c in range(len(lv.comps)):
+        if c in lv.expand:
+            L.append(ind + "D[%d] = R(0);" % c)
+            continue
         ex = dcontrib.get(c)
-        L.append(ind + "D[%d] = %s;" % (c, tree_sum(ex)))
+        neg = dneg.get(c)
+        if neg:
+            L.append(ind + "D[%d] = %s - %s;" % (c, tree_sum(ex) if ex else "R(0)", tree_sum(neg)))
+        else:
+            L.append(ind + "D[%d] = %s;" % (c, tree_sum(ex)))
     L.append(ind + "return E;")
     L.append("  }")
     return L
 
 
-INTERPRET_FROM_LEVEL = 18
 
 
 def emit_contract_program(lv: Level):
@@ -1062,17 +1119,27 @@ def _flops_of(lines):
     return total
 
 
-def flop_counts(lv):
-    """Per-pair and per-atom flop counts of the generated functions."""
-    maxnu = max(lv.nu_max)
-    n_mono = sum(n_sym(n) for n in range(1, maxnu + 1))
-    mom = emit_moments(lv)
-    adj = emit_pair_adjoint(lv)
-    con = emit_contract(lv)
+def flop_counts(lv, sweep_all=False):
+    """Per-pair and per-atom flop counts of the generated functions.  With
+    sweep_all, of the code that sweeps every Cartesian component (the
+    method's operation count as written, without the reduction on the unit
+    sphere)."""
+    saved = lv.expand, lv.swept
+    if sweep_all:
+        lv.expand, lv.swept = {}, list(range(len(lv.comps)))
+    try:
+        keys = {K for c, (mu, K) in enumerate(lv.comps) if c not in lv.expand}
+        n_mono = len(_closure(keys))
+        mom = emit_moments(lv)
+        adj = emit_pair_adjoint(lv)
+        con = emit_contract(lv) if lv.level < INTERPRET_FROM_LEVEL else []
+    finally:
+        lv.expand, lv.swept = saved
     return {
         "monomials": n_mono,
         "moments": _flops_of(mom) - n_mono,
         "pair_adjoint": _flops_of(adj) - n_mono,
         "contract": _flops_of(con),
         "ncomp": len(lv.comps),
+        "nswept": len(lv.comps) if sweep_all else len(lv.swept),
     }
