@@ -33,7 +33,7 @@ FP32_LANES = 128
 # DRAM read + write per atom of efv_kernel<MtpLevel16, float, 0> from the
 # latest ncu capture in profiles/efv_kernel_bcc70_l16_mixed.md (686,000 atoms;
 # traffic scales with the atom count).  Set to None whenever that kernel changes.
-EFV_TRAFFIC_BYTES_PER_ATOM = (185.187840e6 + 148.744192e6) / 686000
+EFV_TRAFFIC_BYTES_PER_ATOM = (184.299520e6 + 11.423744e6) / 686000
 
 
 def _peaks():

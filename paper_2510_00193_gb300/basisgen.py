@@ -684,7 +684,7 @@ def emit_pair_adjoint(lv: Level, subset=None, fname="pair_adjoint"):
     return L
 
 
-def emit_contract(lv: Level):
+def emit_contract(lv: Level, fname="contract"):
     """Per atom: graph values from the DAG, basis products, E = sum xi B, and the
     reverse pass D = dE/dM.  ``WANT_B`` stores the basis values."""
     dag = lv.dag
@@ -693,8 +693,8 @@ def emit_contract(lv: Level):
     # M: the moment components, indexed M[c] (an array, or a strided view of them in shared memory)
     # B: where the basis values go when WANT_B: an array (B[a] = value) or a sink called as B(a, value)
     L.append("  template <class R, bool WANT_B, class MV = const R*, class BV = R*>")
-    L.append("  __device__ __forceinline__ static R contract(MV M, "
-             "const typename ScalarOf<R>::T* __restrict__ xi, R* __restrict__ D, BV B) {")
+    L.append("  __device__ __forceinline__ static R %s(MV M, "
+             "const typename ScalarOf<R>::T* __restrict__ xi, R* __restrict__ D, BV B) {" % fname)
     L.append(ind + "(void)B;")
     # forward.  Components with a z-exponent >= 2 (when the sweeps leave them
     # out) are formed from the swept ones first, in increasing z-exponent.
@@ -844,6 +844,212 @@ def emit_contract(lv: Level):
     return L
 
 
+
+
+def _node_closure(dag, roots):
+    """C nodes and M leaves reachable from the (weight, node) roots."""
+    seen = set()
+    stack = [node for _, node in roots]
+    while stack:
+        n = stack.pop()
+        if n in seen:
+            continue
+        seen.add(n)
+        key = dag.nodes[n][0]
+        if key[0] == "C":
+            stack += [key[1], key[2]]
+    return seen
+
+
+def emit_contract_by_graph(lv: Level, fname="contract"):
+    """Same results as emit_contract (up to rounding order), with the reverse
+    pass run graph by graph: each graph's DAG nodes are formed again from the
+    moments (read through an optimisation barrier, so that the compiler forms
+    them anew instead of keeping the forward pass's values) and their adjoints
+    are added into the D accumulators at once.  Across the reverse pass only
+    the moments, the D accumulators and the graph adjoints stay live, instead
+    of every node value of the DAG."""
+    dag = lv.dag
+    L = []
+    ind = "    "
+    L.append("  template <class R, bool WANT_B, class MV = const R*, class BV = R*>")
+    L.append("  __device__ __forceinline__ static R %s(MV M, "
+             "const typename ScalarOf<R>::T* __restrict__ xi, R* __restrict__ D, BV B) {" % fname)
+    L.append(ind + "(void)B;")
+    exp_order = sorted(lv.expand, key=lambda t: (lv.comps[t][1][2], t))
+
+    def emit_nodes(nodes, mname, sfx):
+        """Forward values of the C nodes in `nodes`; M component c is mname(c)."""
+        wname = {}
+
+        def comp_ref(n, K):
+            key, rank = dag.nodes[n]
+            if key[0] == "M":
+                _, mu, nu, off = key
+                return mname(lv.comp_index[(mu, (off[0] + K[0], off[1] + K[1], off[2] + K[2]))])
+            return "v%d_%d%s" % (n, multi_indices(rank).index(K), sfx)
+
+        for n in sorted(nodes):
+            key, rank = dag.nodes[n]
+            if key[0] != "C":
+                continue
+            _, a, b = key
+            Ps = multi_indices(dag.rank(b))
+            wn = []
+            for j, P in enumerate(Ps):
+                w = multinomial_weight(P)
+                if w == 1:
+                    wn.append(comp_ref(b, P))
+                else:
+                    nm = "w%d_%d%s" % (n, j, sfx)
+                    L.append(ind + "const R %s = R(%d) * %s;" % (nm, w, comp_ref(b, P)))
+                    wn.append(nm)
+            wname[n] = wn
+            for ki, K in enumerate(multi_indices(rank)):
+                terms = [(comp_ref(a, (K[0] + P[0], K[1] + P[1], K[2] + P[2])), wn[j]) for j, P in enumerate(Ps)]
+                emit_dot(L, ind, "v%d_%d%s" % (n, ki, sfx), terms)
+        return comp_ref, wname
+
+    # forward pass: formed moment components, every node, graphs, basis, E
+    for c in exp_order:
+        s0, s1, s2 = (("M[%d]" % t) if t not in lv.expand else ("mx%d" % t) for t in lv.expand[c])
+        L.append(ind + "const R mx%d = (%s - %s) - %s;" % (c, s0, s1, s2))
+    comp_ref, _ = emit_nodes(range(len(dag.nodes)), lambda c: ("mx%d" % c) if c in lv.expand else ("M[%d]" % c), "")
+    for gi, roots in enumerate(lv.roots):
+        parts = []
+        for w, node in roots:
+            ref = comp_ref(node, (0, 0, 0))
+            parts.append(ref if w == 1 else "R(%d) * %s" % (w, ref))
+        L.append(ind + "const R G%d = %s;" % (gi, tree_sum(parts)))
+    L.append(ind + "R E = R(0);")
+    for a, b in enumerate(lv.bases):
+        L.append(ind + "const R B%d = %s;" % (a, " * ".join("G%d" % k for k in b)))
+        L.append(ind + "if (WANT_B) store_basis(B, %d, B%d);" % (a, a))
+        L.append(ind + "E = fmadd(R(xi[%d]), B%d, E);" % (a, a))
+    gbar = defaultdict(list)
+    for a, b in enumerate(lv.bases):
+        for j in range(len(b)):
+            others = [b[t] for t in range(len(b)) if t != j]
+            gbar[b[j]].append((a, others))
+    for gi in range(len(lv.graphs)):
+        terms = []
+        for a, others in gbar[gi]:
+            prod = " * ".join("G%d" % k for k in others)
+            terms.append("R(xi[%d])" % a + (" * " + prod if prod else ""))
+        L.append(ind + "const R Gb%d = %s;" % (gi, tree_sum(terms)))
+    # reverse pass, graph by graph
+    for c in range(len(lv.comps)):
+        L.append(ind + "D[%d] = R(0);" % c)
+    for gi, roots in enumerate(lv.roots):
+        sfx = "_g%d" % gi
+        nodes = _node_closure(dag, roots)
+        # moment components the graph reads (and the swept ones they are formed from)
+        used = set()
+        for n in nodes:
+            key, rank = dag.nodes[n]
+            if key[0] == "M":
+                _, mu, nu, off = key
+                for K in multi_indices(rank):
+                    used.add(lv.comp_index[(mu, (off[0] + K[0], off[1] + K[1], off[2] + K[2]))])
+        stack = list(used)
+        while stack:
+            c = stack.pop()
+            for t in lv.expand.get(c, ()):
+                if t not in used:
+                    used.add(t)
+                    stack.append(t)
+
+        def mname(c, sfx=sfx):
+            return ("mx%d%s" % (c, sfx)) if c in lv.expand else ("m%d%s" % (c, sfx))
+
+        for c in sorted(t for t in used if t not in lv.expand):
+            L.append(ind + "R %s = M[%d];" % (mname(c), c))
+            L.append(ind + "opaque(%s);" % mname(c))
+        for c in exp_order:
+            if c in used:
+                s0, s1, s2 = (mname(t) for t in lv.expand[c])
+                L.append(ind + "const R %s = (%s - %s) - %s;" % (mname(c), s0, s1, s2))
+        cref, wname = emit_nodes(nodes, mname, sfx)
+        adj = defaultdict(list)
+        for w, node in roots:
+            adj[(node, 0)].append("Gb%d" % gi if w == 1 else "R(%d) * Gb%d" % (w, gi))
+        dpos, dneg = defaultdict(list), defaultdict(list)
+        for n in sorted(nodes, reverse=True):
+            key, rank = dag.nodes[n]
+            names = []
+            for ki in range(n_sym(rank)):
+                ex = adj.get((n, ki))
+                if not ex:
+                    names.append(None)
+                    continue
+                nm = "b%d_%d%s" % (n, ki, sfx)
+                L.append(ind + "const R %s = %s;" % (nm, tree_sum(ex)))
+                names.append(nm)
+            if key[0] == "M":
+                _, mu, nu, off = key
+                for ki, K in enumerate(multi_indices(rank)):
+                    if names[ki] is not None:
+                        dpos[lv.comp_index[(mu, (off[0] + K[0], off[1] + K[1], off[2] + K[2]))]].append(names[ki])
+                continue
+            _, a, b = key
+            Ps = multi_indices(dag.rank(b))
+            ra = dag.rank(a)
+            bacc = defaultdict(list)
+            for ki, K in enumerate(multi_indices(rank)):
+                if names[ki] is None:
+                    continue
+                for j, P in enumerate(Ps):
+                    full = (K[0] + P[0], K[1] + P[1], K[2] + P[2])
+                    adj[(a, multi_indices(ra).index(full))].append("%s * %s" % (names[ki], wname[n][j]))
+                    bacc[j].append((names[ki], cref(a, full)))
+            for j, lst in bacc.items():
+                w = multinomial_weight(Ps[j])
+                nm = "c%d_%d%s" % (n, j, sfx)
+                emit_dot(L, ind, nm, lst)
+                adj[(b, j)].append(nm if w == 1 else "R(%d) * %s" % (w, nm))
+        # this graph's adjoints of formed components go to the swept ones
+        for c in sorted(lv.expand, key=lambda t: (-lv.comps[t][1][2], -t)):
+            if not dpos.get(c) and not dneg.get(c):
+                continue
+            nm = "dx%d%s" % (c, sfx)
+            pos = tree_sum(dpos[c]) if dpos.get(c) else "R(0)"
+            L.append(ind + "const R %s = %s;" % (nm, pos if not dneg.get(c) else "%s - %s" % (pos, tree_sum(dneg[c]))))
+            s0, s1, s2 = lv.expand[c]
+            dpos[s0].append(nm)
+            dneg[s1].append(nm)
+            dneg[s2].append(nm)
+        for c in sorted(set(dpos) | set(dneg)):
+            if c in lv.expand:
+                continue
+            ex = "D[%d]" % c
+            if dpos.get(c):
+                ex = "%s + %s" % (ex, tree_sum(dpos[c]))
+            if dneg.get(c):
+                ex = "(%s) - %s" % (ex, tree_sum(dneg[c]))
+            L.append(ind + "D[%d] = %s;" % (c, ex))
+    L.append(ind + "return E;")
+    L.append("  }")
+    return L
+
+
+# Contraction code shape for the straight-line levels in FP32: the reverse
+# pass graph by graph with recomputed nodes (True) or over the whole DAG
+# (False).  FP64 and dual-number code always take the whole-DAG form (the
+# recomputation costs FP64-pipe time: 46.5 against 44.4 ms for the
+# 1,024,000-atom FP64 evaluation).
+CONTRACT_BY_GRAPH = True
+
+
+def emit_contract_dispatch():
+    """contract(): the per-graph form for FP32, the whole-DAG form otherwise."""
+    return ["  template <class R, bool WANT_B, class MV = const R*, class BV = R*>",
+            "  __device__ __forceinline__ static R contract(MV M, "
+            "const typename ScalarOf<R>::T* __restrict__ xi, R* __restrict__ D, BV B) {",
+            "    if constexpr (std::is_same<R, float>::value)",
+            "      return contract_graph<R, WANT_B, MV, BV>(M, xi, D, B);",
+            "    else",
+            "      return contract_dag<R, WANT_B, MV, BV>(M, xi, D, B);",
+            "  }"]
 
 
 def emit_contract_program(lv: Level):
@@ -1019,7 +1225,10 @@ def emit_header(lv: Level):
         out = out[:out.index("struct %s {" % name)] + tables + out[out.index("struct %s {" % name):]
         out += body
     else:
-        out += emit_contract(lv)
+        out += emit_contract(lv, "contract_dag")
+        out += (emit_contract_by_graph(lv, "contract_graph") if CONTRACT_BY_GRAPH
+                else emit_contract(lv, "contract_graph"))
+        out += emit_contract_dispatch()
     out.append("};")
     out.append("}  // namespace mtp")
     return "\n".join(out) + "\n"
@@ -1132,7 +1341,11 @@ def flop_counts(lv, sweep_all=False):
         n_mono = len(_closure(keys))
         mom = emit_moments(lv)
         adj = emit_pair_adjoint(lv)
-        con = emit_contract(lv) if lv.level < INTERPRET_FROM_LEVEL else []
+        # algorithmic count: the whole-DAG contraction; executed (FP32): the
+        # form the FP32 kernels run
+        con = []
+        if lv.level < INTERPRET_FROM_LEVEL:
+            con = (emit_contract_by_graph(lv) if (CONTRACT_BY_GRAPH and not sweep_all) else emit_contract(lv))
     finally:
         lv.expand, lv.swept = saved
     return {

@@ -6,7 +6,12 @@
 // global counter until none are left.  Each item's atoms belong to one
 // configuration, so the block reduces energy, virial and dE/dtheta in shared
 // memory and adds them to that configuration's slots with one FP64 atomic per
-// value.  The per-atom work is the single-configuration code (efv_atom).
+// value.  The per-atom work is the single-configuration code (efv_atom), with
+// the whole-DAG contraction: inside the persistent loop the per-graph form
+// spills more (1.5-1.8 KB against 0.7-0.9 KB per thread at level 16) and
+// measured slower (1.80 against 1.76 ms for the 4096-configuration batch
+// with dE/dtheta; the per-graph form in a non-inlined per-item function needs
+// no stack but took 2.25 ms).
 #pragma once
 #include "efv_kernel.cuh"
 
@@ -49,8 +54,8 @@ __global__ void __launch_bounds__(256) batch_kernel(const BatchArgs b) {
     R w[6] = {R(0), R(0), R(0), R(0), R(0), R(0)};
     const bool active = (int)threadIdx.x < count;
     if (__any_sync(0xffffffffu, active))   // warp-uniform: whole warps without atoms skip the work
-      efv_atom<LV, R, DTHETA, false, NQ>(a, sm, active ? first + threadIdx.x : first, active, s_cell, nullptr, e_i,
-                                         w);
+      efv_atom<LV, R, DTHETA, false, NQ, true>(a, sm, active ? first + threadIdx.x : first, active, s_cell, nullptr,
+                                               e_i, w);
     efv_block_flush<LV, R, DTHETA>(sm, e_i, w, b.e_cfg + cfg, b.virial_cfg + (int64_t)cfg * 6,
                                    DTHETA ? b.dtheta_cfg + (int64_t)cfg * b.n_params : nullptr);
     __syncthreads();

@@ -378,7 +378,9 @@ constexpr int kMaxWarps = 8;   // blocks of up to 256 threads
 
 template <class R, int NMU, bool DTHETA>
 __host__ __device__ __forceinline__ size_t efv_smem_bytes(int SS, int nq, int m) {
-  return efv_red_offset<R, NMU, DTHETA>(SS, nq, m) + sizeof(double) * 8 * kMaxWarps + sizeof(int) * kMaxSpecies;
+  // ... then the per-species atom counts and one 8-byte discard slot
+  return efv_red_offset<R, NMU, DTHETA>(SS, nq, m) + sizeof(double) * 8 * kMaxWarps +
+         ((sizeof(int) * kMaxSpecies + 7) & ~size_t(7)) + sizeof(double);
 }
 
 // Mixed path with DTHETA: each thread's dE/dc accumulators [zj][mu][k] in
@@ -411,6 +413,20 @@ template <class R> struct WarpBasisSink {
   }
 };
 
+// Consumes each basis value as the contraction forms it: lane 0 of the warp
+// writes it to a shared word that nothing reads.  Used where the basis values
+// are not wanted: with a use of this kind the level-16 energy/force kernel
+// compiles without stack (the contraction alone fits in its registers);
+// without one, ptxas keeps values of the contraction live into the adjoint
+// sweep and spills about 1.1 KB per thread.
+template <class R> struct DiscardBasisSink {
+  R* slot;
+  bool lane0;
+  __device__ __forceinline__ void operator()(int, R v) const {
+    if (lane0) *slot = v;
+  }
+};
+
 template <class R> struct AccView {
   R* p;
   int stride;
@@ -428,6 +444,7 @@ struct EfvShared {
   R* acc;     // mixed DTHETA: per-thread dE/dc accumulators [S NMU nq][blockDim], or null
   double* red;
   int* cnt;   // [S]
+  R* discard; // one word that DiscardBasisSink writes and nothing reads
   int S, SS, nq, cstride, m;
   R rcut, mid, scale, rmin;
 
@@ -443,6 +460,7 @@ struct EfvShared {
     dxi = dc + (DTHETA ? SS * NMU * nq : 0);
     red = reinterpret_cast<double*>(raw + efv_red_offset<R, NMU, DTHETA>(SS, nq, m));
     cnt = reinterpret_cast<int*>(red + 8 * kMaxWarps);
+    discard = reinterpret_cast<R*>(red + 8 * kMaxWarps + (sizeof(int) * kMaxSpecies + 7) / 8);
     acc = nullptr;
     if (DTHETA && sizeof(R) == 4 && S <= 4) {
       const size_t off = (efv_smem_bytes<R, NMU, DTHETA>(SS, nq, m) + 15) & ~size_t(15);
@@ -697,7 +715,17 @@ __device__ __forceinline__ void adjoint_sweep(const EfvArgs& a, const EfvShared<
 // and 20: 201 and 295 components) sweep the neighbours once per group, so
 // that a group's moments, then its adjoints, stay in registers; the full
 // vectors meet the interpreter once per atom.
-template <class LV, class R, bool DTHETA, bool PHASE_SYNC = false, int NQ = 0>
+// The contraction of a single-group level: the generated whole-DAG form
+// (DAG) or the default for R (per graph in FP32).
+template <class LV, bool DAG, class R, bool WANT_B, class MV, class BV>
+__device__ __forceinline__ R contract_atom(MV M, const typename ScalarOf<R>::T* __restrict__ xi, R* D, BV B) {
+  if constexpr (DAG)
+    return LV::template contract_dag<R, WANT_B, MV, BV>(M, xi, D, B);
+  else
+    return LV::template contract<R, WANT_B, MV, BV>(M, xi, D, B);
+}
+
+template <class LV, class R, bool DTHETA, bool PHASE_SYNC = false, int NQ = 0, bool DAG = false>
 __device__ __forceinline__ void efv_atom(const EfvArgs& a, const EfvShared<R, LV::NMU, DTHETA>& sm, int64_t i,
                                          bool active, const R* cell, const double* cell64, double& e_i, R* w) {
   constexpr int NMU = LV::NMU;
@@ -734,8 +762,11 @@ __device__ __forceinline__ void efv_atom(const EfvArgs& a, const EfvShared<R, LV
     // dE/dxi: each basis value is summed across the warp as soon as the
     // contraction forms it, so that none of them stays live through the
     // reverse pass
-    ei = LV::template contract<R, true, const R*, WarpBasisSink<R>>(
+    ei = contract_atom<LV, DAG, R, true, const R*, WarpBasisSink<R>>(
         M, sm.xi, D, WarpBasisSink<R>{sm.dxi, (int)(threadIdx.x & 31), active});
+  } else if constexpr (!DTHETA && LV::NGROUPS == 1) {
+    ei = contract_atom<LV, DAG, R, true, const R*, DiscardBasisSink<R>>(
+        M, sm.xi, D, DiscardBasisSink<R>{sm.discard, (threadIdx.x & 31) == 0});
   } else {
     R Bv[DTHETA ? LV::NBASIS : 1];
     ei = LV::template contract<R, DTHETA>(M, sm.xi, D, Bv);

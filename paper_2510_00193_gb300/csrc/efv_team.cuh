@@ -86,7 +86,12 @@ __global__ void __launch_bounds__(kEfvThreads) efv_team_kernel(const EfvArgs a) 
     // contraction (every lane, the same values)
     R D[C];
     R Bv[DTHETA ? LV::NBASIS : 1];
-    const R ei = LV::template contract<R, DTHETA>(M, sm.xi, D, Bv);
+    R ei;
+    if constexpr (DTHETA)
+      ei = LV::template contract<R, true>(M, sm.xi, D, Bv);
+    else
+      ei = LV::template contract<R, true, const R*, DiscardBasisSink<R>>(
+          M, sm.xi, D, DiscardBasisSink<R>{sm.discard, lane == 0});
     if (lane == 0) {
       e_i = a.species_energy[zi] + (double)ei;
       a.e_atom[i] = e_i;

@@ -1,6 +1,7 @@
 // Scalar helpers shared by the generated MTP level code and the kernels.
 #pragma once
 #include <cmath>
+#include <type_traits>
 
 #ifndef __CUDACC__
 #define __device__
@@ -34,6 +35,29 @@ __host__ __device__ __forceinline__ double fmadd(double a, double b, double c) {
 template <class S>
 __host__ __device__ __forceinline__ Dual<S> fmadd(Dual<S> a, Dual<S> b, Dual<S> c) {
   return {fmadd(a.v, b.v, c.v), fmadd(a.v, b.t, fmadd(a.t, b.v, c.t))};
+}
+
+// Optimisation barrier: afterwards the compiler must treat x as an unknown
+// value, so expressions of it are formed anew rather than merged with the same
+// expressions of the value before (the generated contraction uses this to
+// recompute DAG nodes in its reverse pass instead of keeping them live).
+__host__ __device__ __forceinline__ void opaque(float& x) {
+#ifdef __CUDA_ARCH__
+  asm volatile("" : "+f"(x));
+#else
+  (void)x;
+#endif
+}
+__host__ __device__ __forceinline__ void opaque(double& x) {
+#ifdef __CUDA_ARCH__
+  asm volatile("" : "+d"(x));
+#else
+  (void)x;
+#endif
+}
+template <class S> __host__ __device__ __forceinline__ void opaque(Dual<S>& x) {
+  opaque(x.v);
+  opaque(x.t);
 }
 
 // Where the contraction puts basis value a: an array, or a sink object
