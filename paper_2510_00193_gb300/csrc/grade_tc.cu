@@ -39,8 +39,9 @@
 // Kernel layout (tc_grade_kernel): one CTA per SM, persistent over 128-row
 // tiles, one column half (64 of the padded 128 columns) per CTA.  Shared
 // memory holds the 7 Y slices of the half (7 x 16 KB, loaded once by bulk
-// copies) and a double buffer of X slices (2 x 32 KB, streamed by 1-D bulk
-// copies through the TMA engine).  Warp 0: copy producer; warp 1: Tensor
+// copies) and three X slice buffers (3 x 32 KB, streamed by 1-D bulk copies
+// through the TMA engine; with two, the copy latency was exposed on the later
+// slices, which carry few MMAs).  Warp 0: copy producer; warp 1: Tensor
 // Memory allocation and the MMA issuer (one thread); warps 2-5: epilogue, one
 // TMEM lane (tile row) per thread.  Seven FP32 accumulators of 64 columns
 // occupy 448 of the 512 TMEM columns.  Operands use the no-swizzle K-major
@@ -65,7 +66,7 @@ constexpr int kTcDmax = 8;                // slice pairs with s + t <= kTcDmax
 constexpr int kTcNacc = kTcDmax - 1;      // accumulators G_2 .. G_8
 constexpr uint32_t kXBytes = kTcM * kTcK * 2;   // one X slice tile, BF16
 constexpr uint32_t kYBytes = kTcN * kTcK * 2;   // one Y slice half, BF16
-constexpr int kXBufs = 2;
+constexpr int kXBufs = 3;
 constexpr int kTcThreads = 192;
 constexpr uint32_t kTmemCols = 512;
 constexpr uint64_t kTcTimeoutNs = 1000000000ull;  // 1 s per wait
@@ -91,10 +92,10 @@ __host__ __device__ __forceinline__ int64_t y_elem(int k, int j) {
 }
 
 // Shared-memory map of tc_grade_kernel (bytes).
-constexpr uint32_t kSmY = 0;
-constexpr uint32_t kSmX = kSmY + kTcS * kYBytes;            // 114688
-constexpr uint32_t kSmBar = kSmX + kXBufs * kXBytes;        // 180224
-constexpr int kNumBars = 8;   // y_full, x_full[2], x_empty[2], acc_full, acc_empty, drain
+constexpr uint32_t kSmX = 0;
+constexpr uint32_t kSmY = kSmX + kXBufs * kXBytes;          // 98304
+constexpr uint32_t kSmBar = kSmY + kTcS * kYBytes;          // 212992
+constexpr int kNumBars = 4 + 2 * kXBufs;   // y_full, x_full[kXBufs], x_empty[kXBufs], acc_full, acc_empty, drain
 constexpr uint32_t kSmSlot = kSmBar + 8 * kNumBars;         // TMEM base address
 constexpr uint32_t kSmAbort = kSmSlot + 4;
 constexpr uint32_t kSmFexp = kSmAbort + 4;                  // int [64]
@@ -102,9 +103,17 @@ constexpr uint32_t kSmTotal = kSmFexp + 4 * kTcN;
 // The block takes the whole 227 KB a block may have: one block per SM (the
 // 512 TMEM columns are this block's alone), and every operand descriptor,
 // whichever of its two strides the hardware applies to rows or to K, stays
-// inside the allocation (worst case 207,104 bytes).
+// inside the allocation (worst cases: X buffer 2 at 65,536 + 59,648 =
+// 125,184 bytes; Y slice 6 at 196,608 + 14,336 + 7,424 = 218,368 bytes).
 constexpr uint32_t kSmAlloc = 232448;
 static_assert(kSmTotal <= kSmAlloc, "shared-memory map exceeds the allocation");
+// furthest byte an operand descriptor could reach with its strides swapped:
+// last X buffer, last K step, 16 row groups at LBO and 2 K core matrices at SBO
+static_assert(kSmX + (kXBufs - 1) * kXBytes + (kTcK / 16 - 1) * 2 * kXLbo + 15 * kXLbo + kXSbo + 128 <= kSmAlloc,
+              "X operand descriptors may leave the allocation");
+// last Y slice, last K step, 8 row groups at LBO and 2 K core matrices at SBO
+static_assert(kSmY + (kTcS - 1) * kYBytes + (kTcK / 16 - 1) * 2 * kYLbo + 7 * kYLbo + kYSbo + 128 <= kSmAlloc,
+              "Y operand descriptors may leave the allocation");
 
 constexpr int kBadRow = INT_MAX;   // erow sentinel: non-finite basis row
 
@@ -300,17 +309,17 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_grade_kernel(const TcGemmArg
   const uint32_t x_sm = tc::smem_addr(sm + kSmX);
   const uint32_t b_yfull = tc::smem_addr(&bars[0]);
   const uint32_t b_xfull0 = tc::smem_addr(&bars[1]);
-  const uint32_t b_xempty0 = tc::smem_addr(&bars[3]);
-  const uint32_t b_accfull = tc::smem_addr(&bars[5]);
-  const uint32_t b_accempty = tc::smem_addr(&bars[6]);
-  const uint32_t b_drain = tc::smem_addr(&bars[7]);
+  const uint32_t b_xempty0 = tc::smem_addr(&bars[1 + kXBufs]);
+  const uint32_t b_accfull = tc::smem_addr(&bars[1 + 2 * kXBufs]);
+  const uint32_t b_accempty = tc::smem_addr(&bars[2 + 2 * kXBufs]);
+  const uint32_t b_drain = tc::smem_addr(&bars[3 + 2 * kXBufs]);
 
   if (threadIdx.x == 0) {
     tc::mbar_init(b_yfull, 1);
-    tc::mbar_init(b_xfull0, 1);
-    tc::mbar_init(b_xfull0 + 8, 1);
-    tc::mbar_init(b_xempty0, 1);
-    tc::mbar_init(b_xempty0 + 8, 1);
+    for (int b = 0; b < kXBufs; ++b) {
+      tc::mbar_init(b_xfull0 + 8 * b, 1);
+      tc::mbar_init(b_xempty0 + 8 * b, 1);
+    }
     tc::mbar_init(b_accfull, 1);
     tc::mbar_init(b_accempty, 128);
     tc::mbar_init(b_drain, 1);
@@ -337,8 +346,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_grade_kernel(const TcGemmArg
       int it = 0;
       for (int tile = cta; ok && tile < p.n_tiles; tile += n_cta) {
         for (int s = 0; s < kTcS; ++s, ++it) {
-          const int buf = it & 1;
-          const uint32_t ph = (uint32_t)(it >> 1) & 1u;
+          const int buf = it % kXBufs;
+          const uint32_t ph = (uint32_t)(it / kXBufs) & 1u;
           if (!tc::mbar_wait(b_xempty0 + 8 * buf, ph ^ 1u, abort_flag, p.wait_ns)) {
             ok = false;
             break;
@@ -355,11 +364,11 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_grade_kernel(const TcGemmArg
       // no copy may still be in flight when the block exits
       int never = 0;
       tc::mbar_wait(b_yfull, 0u, &never, kTcTimeoutNs);
-      for (int k = (it > 2 ? it - 2 : 0); k < it; ++k)
-        tc::mbar_wait(b_xfull0 + 8 * (k & 1), (uint32_t)(k >> 1) & 1u, &never, kTcTimeoutNs);
+      for (int k = (it > kXBufs ? it - kXBufs : 0); k < it; ++k)
+        tc::mbar_wait(b_xfull0 + 8 * (k % kXBufs), (uint32_t)(k / kXBufs) & 1u, &never, kTcTimeoutNs);
       if (ok)
-        for (int k = (it > 2 ? it - 2 : 0); k < it; ++k)
-          tc::mbar_wait(b_xempty0 + 8 * (k & 1), (uint32_t)(k >> 1) & 1u, abort_flag, kTcTimeoutNs);
+        for (int k = (it > kXBufs ? it - kXBufs : 0); k < it; ++k)
+          tc::mbar_wait(b_xempty0 + 8 * (k % kXBufs), (uint32_t)(k / kXBufs) & 1u, abort_flag, kTcTimeoutNs);
     }
   } else if (warp == 1) {
     if (lane == 0) {
@@ -375,8 +384,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_grade_kernel(const TcGemmArg
         }
         tc::fence_after_sync();
         for (int s = 0; s < kTcS; ++s, ++it) {
-          const int buf = it & 1;
-          const uint32_t ph = (uint32_t)(it >> 1) & 1u;
+          const int buf = it % kXBufs;
+          const uint32_t ph = (uint32_t)(it / kXBufs) & 1u;
           if (!tc::mbar_wait(b_xfull0 + 8 * buf, ph, abort_flag, p.wait_ns)) {
             ok = false;
             break;
