@@ -237,8 +237,9 @@ int mtp_grade_rows(const double* rows_dev, int64_t n_rows, int64_t ld, const int
  *   xs_dev: BF16 bit patterns, [ceil(n_rows/128)][7][128 x 128] X slices in
  *     the kernel's operand layout: element (row i, column j) of a tile at
  *     (j/8)*1024 + (i/8)*64 + (i%8)*8 + j%8;
- *   ys_dev: [2][7][64 x 128] Y slices, element (column k, row j) of a half
- *     at (j/8)*512 + (k/8)*64 + (k%8)*8 + j%8;
+ *   ys_dev: [2][448 x 128] Y slices, per column half one operand whose row
+ *     kg = 64 t + k is column k of slice t: element (kg, row j) at
+ *     (j/8)*3584 + (kg/8)*64 + (kg%8)*8 + j%8;
  *   fexp_dev [128] column exponents, erow_dev [n_rows] row exponents.
  * Outputs (DEVICE): acc_dev (nullable) [n_rows][2][7][64] FP32 slice-group
  * sums G_d = sum_{s+t=d} X_s Y_t for d = 2..8 per column half;

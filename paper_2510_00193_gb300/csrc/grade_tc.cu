@@ -19,7 +19,11 @@
 //      for y with Y_t.  Integers of at most 8 significant bits are exact in
 //      BF16.
 //   4. Groups: G_d = sum_{s+t=d} X_s Y_t for d = 2..8 (28 products of
-//      128 x 64 x 128 per tile and column half).  Every product of two slices
+//      128 x 64 x 128 per tile and column half; the products of one X slice
+//      with consecutive Y slices are single MMAs of up to 256 columns, since
+//      their accumulators are adjacent in Tensor Memory and the Y slices of a
+//      half form one 448-row operand: 80 MMA instructions per tile instead
+//      of 224).  Every product of two slices
 //      is an integer below 2^16 and every partial sum of a group stays below
 //      2^24 for d <= 7 (|X_1 Y_1| <= 2^16 per term, the later slices at most
 //      half as large each), so the FP32 accumulation in Tensor Memory is exact;
@@ -80,15 +84,18 @@ static uint64_t g_tc_wait_ns = kTcTimeoutNs;
 // i.e. core matrices of 8 rows x 16 bytes, LBO (K direction) 2048 bytes,
 // SBO (row groups) 128 bytes.
 constexpr uint32_t kXLbo = 2048, kXSbo = 128;
-// Y slice layout inside one [64 columns][128 K] half:
-// element (k, j) at (j / 8) * 512 + (k / 8) * 64 + (k % 8) * 8 + j % 8.
-constexpr uint32_t kYLbo = 1024, kYSbo = 128;
+// Y slices of a half: one [448 rows][128 K] operand, row kg = 64 t + k for
+// column k of slice t: element (kg, j) at (j / 8) * 3584 + (kg / 8) * 64 +
+// (kg % 8) * 8 + j % 8, i.e. core matrices of 8 rows x 16 bytes, LBO (K
+// direction) 7168 bytes, SBO (row groups) 128 bytes.
+constexpr uint32_t kYRows = kTcS * kTcN;                       // 448
+constexpr uint32_t kYLbo = (kYRows / 8) * 128, kYSbo = 128;   // 7168, 128
 
 __host__ __device__ __forceinline__ int64_t x_elem(int i, int j) {
   return (int64_t)(j >> 3) * 1024 + (i >> 3) * 64 + (i & 7) * 8 + (j & 7);
 }
-__host__ __device__ __forceinline__ int64_t y_elem(int k, int j) {
-  return (int64_t)(j >> 3) * 512 + (k >> 3) * 64 + (k & 7) * 8 + (j & 7);
+__host__ __device__ __forceinline__ int64_t y_elem(int kg, int j) {
+  return (int64_t)(j >> 3) * (kYRows * 8) + (kg >> 3) * 64 + (kg & 7) * 8 + (j & 7);
 }
 
 // Shared-memory map of tc_grade_kernel (bytes).
@@ -111,9 +118,13 @@ static_assert(kSmTotal <= kSmAlloc, "shared-memory map exceeds the allocation");
 // last X buffer, last K step, 16 row groups at LBO and 2 K core matrices at SBO
 static_assert(kSmX + (kXBufs - 1) * kXBytes + (kTcK / 16 - 1) * 2 * kXLbo + 15 * kXLbo + kXSbo + 128 <= kSmAlloc,
               "X operand descriptors may leave the allocation");
-// last Y slice, last K step, 8 row groups at LBO and 2 K core matrices at SBO
-static_assert(kSmY + (kTcS - 1) * kYBytes + (kTcK / 16 - 1) * 2 * kYLbo + 7 * kYLbo + kYSbo + 128 <= kSmAlloc,
-              "Y operand descriptors may leave the allocation");
+// Y operands (runs of up to 4 slices starting at slice 0 or 4), last K step:
+// row groups at SBO, the second K core matrix at LBO; inside the Y region
+static_assert(kSmY + (kTcK / 16 - 1) * 2 * kYLbo + (4 * kTcN / 8 - 1) * kYSbo + kYLbo + 128 <= kSmBar,
+              "Y operand (slices 0-3) leaves the Y region");
+static_assert(kSmY + 4 * (kTcN / 8) * kYSbo + (kTcK / 16 - 1) * 2 * kYLbo + (3 * kTcN / 8 - 1) * kYSbo + kYLbo +
+                      128 <= kSmBar,
+              "Y operand (slices 4-6) leaves the Y region");
 
 constexpr int kBadRow = INT_MAX;   // erow sentinel: non-finite basis row
 
@@ -199,7 +210,7 @@ __global__ void tc_dexp_kernel(const double* __restrict__ amax, const unsigned l
 }
 
 // Column exponent f_k (|A^-1_jk| 2^(-d_j - f_k) < 1 for all j) and the BF16
-// slices of y_jk = A^-1_jk 2^(-d_j - f_k), written as [half][t][64 x 128] in
+// slices of y_jk = A^-1_jk 2^(-d_j - f_k), written as [half][448 x 128] in
 // the Y layout.  One block per column k, one thread per row j.
 __global__ void __launch_bounds__(kTcK) tc_prep_y_kernel(const double* __restrict__ a_inv, int m,
                                                          const int* __restrict__ dexp, uint16_t* __restrict__ ys,
@@ -230,7 +241,8 @@ __global__ void __launch_bounds__(kTcK) tc_prep_y_kernel(const double* __restric
   balanced_digits(F, q);
   const int half = k / kTcN, kl = k % kTcN;
 #pragma unroll
-  for (int s = 0; s < kTcS; ++s) ys[(int64_t)(half * kTcS + s) * (kTcN * kTcK) + y_elem(kl, j)] = (uint16_t)q[s];
+  for (int s = 0; s < kTcS; ++s)
+    ys[(int64_t)half * (kYRows * kTcK) + y_elem(s * kTcN + kl, j)] = (uint16_t)q[s];
 }
 
 // Row exponents e_i and the BF16 slices of x = b D 2^-e, written as
@@ -373,7 +385,9 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_grade_kernel(const TcGemmArg
   } else if (warp == 1) {
     if (lane == 0) {
       // ---- MMA issuer ----
-      constexpr uint32_t idesc = tc::idesc_bf16_f32(kTcM, kTcN);
+      // instruction descriptors for runs of 1..4 Y slices (N = 64..256)
+      constexpr uint32_t idesc1 = tc::idesc_bf16_f32(kTcM, kTcN), idesc2 = tc::idesc_bf16_f32(kTcM, 2 * kTcN),
+                         idesc3 = tc::idesc_bf16_f32(kTcM, 3 * kTcN), idesc4 = tc::idesc_bf16_f32(kTcM, 4 * kTcN);
       bool ok = tc::mbar_wait(b_yfull, 0u, abort_flag, p.wait_ns);
       tc::fence_after_sync();
       int it = 0, tcount = 0;
@@ -392,9 +406,13 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_grade_kernel(const TcGemmArg
           }
           tc::fence_after_sync();
           const uint32_t xa = x_sm + buf * kXBytes;
-          for (int t = 0; s + t <= kTcDmax - 2; ++t) {
-            const uint32_t d_tmem = tmem + (uint32_t)((s + t) * kTcN);
-            const uint32_t yb = y_sm + t * kYBytes;
+          // X_s Y_t for t = 0 .. 6 - s, as runs of up to 4 consecutive Y
+          // slices: accumulators G_{s+t} .. are adjacent TMEM columns
+          for (int t0 = 0; t0 <= kTcDmax - 2 - s; t0 += 4) {
+            const int cnt = min(4, kTcDmax - 1 - s - t0);
+            const uint32_t idesc = cnt == 4 ? idesc4 : cnt == 3 ? idesc3 : cnt == 2 ? idesc2 : idesc1;
+            const uint32_t d_tmem = tmem + (uint32_t)((s + t0) * kTcN);
+            const uint32_t yb = y_sm + (uint32_t)t0 * (kTcN / 8) * kYSbo;
 #pragma unroll
             for (int kk = 0; kk < kTcK / 16; ++kk) {
               tc::mma_bf16(d_tmem, tc::smem_desc(xa + kk * 2 * kXLbo, kXLbo, kXSbo),

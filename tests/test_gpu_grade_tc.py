@@ -51,15 +51,17 @@ def pack_x(X):
 
 
 def pack_y(Y):
-    """[S, 128 (j), 128 (k)] -> [2 halves][S][64 x 128]: element (k, j) of a
-    half at (j/8)*512 + (k/8)*64 + (k%8)*8 + j%8."""
-    out = np.zeros((2, N_SLICES, 64 * K), dtype=np.uint16)
-    k = np.arange(64)[:, None]
+    """[S, 128 (j), 128 (k)] -> [2 halves][S * 64 x 128]: per half one operand
+    whose row kg = 64 s + k is column k of slice s; element (kg, j) at
+    (j/8)*(8 * 64 S) + (kg/8)*64 + (kg%8)*8 + j%8."""
+    rows = N_SLICES * 64
+    out = np.zeros((2, rows * K), dtype=np.uint16)
+    kg = np.arange(rows)[:, None]
     j = np.arange(K)[None, :]
-    pos = (j // 8) * 512 + (k // 8) * 64 + (k % 8) * 8 + j % 8
+    pos = (j // 8) * (8 * rows) + (kg // 8) * 64 + (kg % 8) * 8 + j % 8
     for h in range(2):
-        for s in range(N_SLICES):
-            out[h, s, pos.ravel()] = bf16_bits(Y[s][:, h * 64:(h + 1) * 64].T).ravel()
+        blk = np.concatenate([Y[s][:, h * 64:(h + 1) * 64].T for s in range(N_SLICES)], axis=0)   # [rows, K]
+        out[h, pos.ravel()] = bf16_bits(blk).ravel()
     return out
 
 
