@@ -107,18 +107,25 @@ __global__ void bin_count_kernel(const double* __restrict__ sw, int64_t n, NbrGe
   atomicAdd(bin_count + b, 1);
 }
 
+// Atoms in bin order, with their FP32 wrapped positions beside them (the
+// candidate loops read both by slot, without a dependent gather).
 __global__ void bin_fill_kernel(const int* __restrict__ bin_of, int64_t n, const int* __restrict__ bin_start,
-                                int* __restrict__ cursor, int* __restrict__ bin_atoms) {
+                                int* __restrict__ cursor, const float4* __restrict__ xw, int* __restrict__ bin_atoms,
+                                float4* __restrict__ bin_xw) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   const int b = bin_of[i];
-  const int slot = atomicAdd(cursor + b, 1);
-  bin_atoms[bin_start[b] + slot] = (int)i;
+  const int slot = bin_start[b] + atomicAdd(cursor + b, 1);
+  bin_atoms[slot] = (int)i;
+  bin_xw[slot] = xw[i];
 }
 
 __device__ __forceinline__ int floor_div(int t, int m) { return t >= 0 ? t / m : -((-t + m - 1) / m); }
 
-// Visits every (j, n) within the cutoff of atom i; FILL writes them.
+// Visits every (j, n) within the cutoff of atom i; FILL writes them.  Along
+// the last axis the searched bins of one (t0, t1) row are consecutive bin
+// indices between wraps, so their atoms are one range of slots: the loop runs
+// over such ranges (one per wrap q2) instead of bin by bin.
 // A candidate passes to the exact FP64 test only if its FP32 squared distance
 // (wrapped positions plus the bin wrap) is below rc2_hi, which exceeds R_cut^2
 // by more than the FP32 rounding can move it, so no pair within the cutoff is
@@ -127,6 +134,7 @@ template <bool FILL>
 __global__ void pair_kernel(const double* __restrict__ x, const double* __restrict__ sw, const int* __restrict__ wrapcnt,
                             const float4* __restrict__ xw, int64_t n, NbrGeom g, const int* __restrict__ bin_start,
                             const int* __restrict__ bin_count, const int* __restrict__ bin_atoms,
+                            const float4* __restrict__ bin_xw,
                             int* __restrict__ counts, const int64_t* __restrict__ offsets, int32_t* __restrict__ out_j,
                             int32_t* __restrict__ out_img, int* __restrict__ status) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -145,22 +153,31 @@ __global__ void pair_kernel(const double* __restrict__ x, const double* __restri
       int q1 = 0, c1 = t1;
       if (g.pbc[1]) { q1 = floor_div(t1, g.nb[1]); c1 = t1 - q1 * g.nb[1]; }
       else if (t1 < 0 || t1 >= g.nb[1]) continue;
-      for (int t2 = bi[2] - g.reach[2]; t2 <= bi[2] + g.reach[2]; ++t2) {
+      int t2 = bi[2] - g.reach[2];
+      int t2_hi = bi[2] + g.reach[2];
+      if (!g.pbc[2]) {
+        t2 = max(t2, 0);
+        t2_hi = min(t2_hi, g.nb[2] - 1);
+      }
+      const int row = (c0 * g.nb[1] + c1) * g.nb[2];
+      while (t2 <= t2_hi) {
         int q2 = 0, c2 = t2;
         if (g.pbc[2]) { q2 = floor_div(t2, g.nb[2]); c2 = t2 - q2 * g.nb[2]; }
-        else if (t2 < 0 || t2 >= g.nb[2]) continue;
-        const int b = (c0 * g.nb[1] + c1) * g.nb[2] + c2;
-        const int s0 = bin_start[b], cnt = bin_count[b];
+        // bins c2 .. c2_end of this row share the wrap q2
+        const int c2_end = min(g.nb[2] - 1, c2 + (t2_hi - t2));
+        const int s_beg = bin_start[row + c2];
+        const int s_end = bin_start[row + c2_end] + bin_count[row + c2_end];
+        t2 += c2_end - c2 + 1;
         const float fq0 = (float)q0, fq1 = (float)q1, fq2 = (float)q2;
         const float shx = fq0 * g.cellf[0] + fq1 * g.cellf[3] + fq2 * g.cellf[6] - pw.x;
         const float shy = fq0 * g.cellf[1] + fq1 * g.cellf[4] + fq2 * g.cellf[7] - pw.y;
         const float shz = fq0 * g.cellf[2] + fq1 * g.cellf[5] + fq2 * g.cellf[8] - pw.z;
-        for (int u = 0; u < cnt; ++u) {
-          const int j = bin_atoms[s0 + u];
-          const float4 qw = xw[j];
+        for (int u = s_beg; u < s_end; ++u) {
+          const float4 qw = bin_xw[u];
           const float fx = qw.x + shx, fy = qw.y + shy, fz = qw.z + shz;
           const float r2f = fx * fx + fy * fy + fz * fz;
           if (r2f >= g.rc2_hi) continue;
+          const int j = bin_atoms[u];
           // image of j relative to the unwrapped positions
           const int n1 = q0 + wi[0] - wrapcnt[3 * j];
           const int n2 = q1 + wi[1] - wrapcnt[3 * j + 1];
@@ -194,28 +211,102 @@ __global__ void pair_kernel(const double* __restrict__ x, const double* __restri
       }
     }
   }
-  if (!FILL) {
-    counts[i] = found;
-    return;
+  if (!FILL) counts[i] = found;
+  // FILL leaves the segment in search order; sort_rows_kernel orders it
+}
+
+// Canonical order of a list entry, (j, n1, n2, n3) lexicographic, as an
+// unsigned key; every field is non-negative once biased.
+__device__ __forceinline__ unsigned long long row_key(int32_t j, int32_t img) {
+  const uint32_t u = (uint32_t)img;
+  return ((unsigned long long)(uint32_t)j << 30) | ((unsigned long long)(u & 1023u) << 20) |
+         ((unsigned long long)((u >> 10) & 1023u) << 10) | (unsigned long long)((u >> 20) & 1023u);
+}
+__device__ __forceinline__ void key_entry(unsigned long long key, int32_t& j, int32_t& img) {
+  j = (int32_t)(key >> 30);
+  const uint32_t n1 = (uint32_t)(key >> 20) & 1023u, n2 = (uint32_t)(key >> 10) & 1023u, n3 = (uint32_t)key & 1023u;
+  img = (int32_t)(n1 | (n2 << 10) | (n3 << 20));
+}
+
+// Bitonic sort of one segment of at most 32 R entries held by a warp, entry
+// e = 32 r + lane in register r of lane `lane` (padding: the largest key).
+template <int R>
+__device__ __forceinline__ void warp_sort_segment(int32_t* __restrict__ out_j, int32_t* __restrict__ out_img,
+                                                  int64_t base, int cnt, int lane) {
+  constexpr int E = 32 * R;
+  unsigned long long v[R];
+#pragma unroll
+  for (int r = 0; r < R; ++r) {
+    const int e = 32 * r + lane;
+    v[r] = e < cnt ? row_key(out_j[base + e], out_img[base + e]) : ~0ull;
   }
-  // canonical order inside the atom's segment: (j, n1, n2, n3)
-  auto key = [](int32_t j, int32_t img) -> long long {
-    int a, b, c;
-    unpack_image(img, a, b, c);
-    return ((long long)j << 30) | ((long long)(a + kImageBias) << 20) | ((long long)(b + kImageBias) << 10) |
-           (long long)(c + kImageBias);
-  };
-  for (int p = 1; p < found; ++p) {
-    const int32_t jj = out_j[base + p], im = out_img[base + p];
-    const long long kp = key(jj, im);
-    int q = p - 1;
-    while (q >= 0 && key(out_j[base + q], out_img[base + q]) > kp) {
-      out_j[base + q + 1] = out_j[base + q];
-      out_img[base + q + 1] = out_img[base + q];
-      --q;
+#pragma unroll
+  for (int k = 2; k <= E; k <<= 1) {
+#pragma unroll
+    for (int j = k >> 1; j > 0; j >>= 1) {
+      if (j >= 32) {
+        const int rj = j >> 5;
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+          if (r & rj) continue;
+          const int e = 32 * r + lane;
+          const unsigned long long a = v[r], b = v[r | rj];
+          const bool asc = (e & k) == 0;
+          v[r] = asc ? (a < b ? a : b) : (a < b ? b : a);
+          v[r | rj] = asc ? (a < b ? b : a) : (a < b ? a : b);
+        }
+      } else {
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+          const int e = 32 * r + lane;
+          const unsigned long long p = __shfl_xor_sync(0xffffffffu, v[r], j);
+          const bool keep_min = ((e & k) == 0) == ((lane & j) == 0);
+          v[r] = keep_min ? (v[r] < p ? v[r] : p) : (v[r] < p ? p : v[r]);
+        }
+      }
     }
-    out_j[base + q + 1] = jj;
-    out_img[base + q + 1] = im;
+  }
+#pragma unroll
+  for (int r = 0; r < R; ++r) {
+    const int e = 32 * r + lane;
+    if (e < cnt) {
+      int32_t jj, im;
+      key_entry(v[r], jj, im);
+      out_j[base + e] = jj;
+      out_img[base + e] = im;
+    }
+  }
+}
+
+// One warp per atom: its list segment into canonical order (j, n1, n2, n3).
+// Segments of up to 256 entries are sorted in registers; longer ones (never
+// at the densities here) by insertion, on lane 0.
+__global__ void sort_rows_kernel(int64_t n, const int64_t* __restrict__ offsets, int32_t* __restrict__ out_j,
+                                 int32_t* __restrict__ out_img) {
+  const int lane = threadIdx.x & 31;
+  const int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  if (i >= n) return;   // warp-uniform
+  const int64_t base = offsets[i];
+  const int64_t cnt64 = offsets[i + 1] - base;
+  if (cnt64 <= 1) return;
+  const int cnt = (int)cnt64;
+  if (cnt64 <= 32) warp_sort_segment<1>(out_j, out_img, base, cnt, lane);
+  else if (cnt64 <= 64) warp_sort_segment<2>(out_j, out_img, base, cnt, lane);
+  else if (cnt64 <= 128) warp_sort_segment<4>(out_j, out_img, base, cnt, lane);
+  else if (cnt64 <= 256) warp_sort_segment<8>(out_j, out_img, base, cnt, lane);
+  else if (lane == 0) {
+    for (int64_t p = 1; p < cnt64; ++p) {
+      const int32_t jj = out_j[base + p], im = out_img[base + p];
+      const unsigned long long kp = row_key(jj, im);
+      int64_t q = p - 1;
+      while (q >= 0 && row_key(out_j[base + q], out_img[base + q]) > kp) {
+        out_j[base + q + 1] = out_j[base + q];
+        out_img[base + q + 1] = out_img[base + q];
+        --q;
+      }
+      out_j[base + q + 1] = jj;
+      out_img[base + q + 1] = im;
+    }
   }
 }
 
@@ -349,9 +440,11 @@ int build_neighbors(mtp_nlist* nl, const double* x, int64_t n, const double* cel
   int* cursor = bin_count + nbins;
   if ((rc = nl->bin_start.ensure(sizeof(int) * (nbins + 1))) != MTP_OK) return rc;
   int* bin_start = nl->bin_start.as<int>();
-  if ((rc = nl->bin_atoms.ensure(sizeof(int) * 2 * std::max<int64_t>(n, 1))) != MTP_OK) return rc;
+  const size_t bin_xw_off = (sizeof(int) * 2 * (size_t)std::max<int64_t>(n, 1) + 15) & ~size_t(15);
+  if ((rc = nl->bin_atoms.ensure(bin_xw_off + sizeof(float4) * (size_t)std::max<int64_t>(n, 1))) != MTP_OK) return rc;
   int* bin_of = nl->bin_atoms.as<int>();
   int* bin_atoms = bin_of + std::max<int64_t>(n, 1);
+  float4* bin_xw = reinterpret_cast<float4*>(reinterpret_cast<char*>(nl->bin_atoms.ptr) + bin_xw_off);
   MTP_TRY_CUDA(cudaMemsetAsync(bin_count, 0, sizeof(int) * 2 * nbins, stream));
   if (n > 0) bin_count_kernel<<<blocks, T, 0, stream>>>(sw, n, g, bin_of, bin_count);
   MTP_TRY_CUDA(cudaGetLastError());
@@ -368,10 +461,10 @@ int build_neighbors(mtp_nlist* nl, const double* x, int64_t n, const double* cel
                                                  ~uintptr_t(15));
   void* tmp = counts64 + n + 2;
   MTP_TRY_CUDA(cub::DeviceScan::ExclusiveSum(tmp, tmp_bytes, bin_count, bin_start, (int)nbins, stream));
-  if (n > 0) bin_fill_kernel<<<blocks, T, 0, stream>>>(bin_of, n, bin_start, cursor, bin_atoms);
+  if (n > 0) bin_fill_kernel<<<blocks, T, 0, stream>>>(bin_of, n, bin_start, cursor, xw, bin_atoms, bin_xw);
   MTP_TRY_CUDA(cudaGetLastError());
   if (n > 0)
-    pair_kernel<false><<<blocks, T, 0, stream>>>(x, sw, wrapcnt, xw, n, g, bin_start, bin_count, bin_atoms, counts, nullptr,
+    pair_kernel<false><<<blocks, T, 0, stream>>>(x, sw, wrapcnt, xw, n, g, bin_start, bin_count, bin_atoms, bin_xw, counts, nullptr,
                                                  nullptr, nullptr, status);
   MTP_TRY_CUDA(cudaGetLastError());
   if ((rc = nl->offsets.ensure(sizeof(int64_t) * (n + 1))) != MTP_OK) return rc;
@@ -391,9 +484,13 @@ int build_neighbors(mtp_nlist* nl, const double* x, int64_t n, const double* cel
   nl->n_pairs = total;
   if ((rc = nl->nbr_j.ensure(sizeof(int32_t) * std::max<int64_t>(total, 1))) != MTP_OK) return rc;
   if ((rc = nl->nbr_img.ensure(sizeof(int32_t) * std::max<int64_t>(total, 1))) != MTP_OK) return rc;
-  if (n > 0)
-    pair_kernel<true><<<blocks, T, 0, stream>>>(x, sw, wrapcnt, xw, n, g, bin_start, bin_count, bin_atoms, nullptr, offsets,
+  if (n > 0) {
+    pair_kernel<true><<<blocks, T, 0, stream>>>(x, sw, wrapcnt, xw, n, g, bin_start, bin_count, bin_atoms, bin_xw, nullptr, offsets,
                                                 nl->nbr_j.as<int32_t>(), nl->nbr_img.as<int32_t>(), status);
+    MTP_TRY_CUDA(cudaGetLastError());
+    sort_rows_kernel<<<(unsigned)((32 * n + T - 1) / T), T, 0, stream>>>(n, offsets, nl->nbr_j.as<int32_t>(),
+                                                                        nl->nbr_img.as<int32_t>());
+  }
   MTP_TRY_CUDA(cudaGetLastError());
   return MTP_OK;
 }
