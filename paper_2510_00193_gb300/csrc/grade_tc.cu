@@ -44,11 +44,13 @@
 // tiles, one column half (64 of the padded 128 columns) per CTA.  Shared
 // memory holds the 7 Y slices of the half (7 x 16 KB, loaded once by bulk
 // copies) and three X slice buffers (3 x 32 KB, streamed by 1-D bulk copies
-// through the TMA engine; with two, the copy latency was exposed on the later
-// slices, which carry few MMAs).  Warp 0: copy producer; warp 1: Tensor
-// Memory allocation and the MMA issuer (one thread); warps 2-5: epilogue, one
-// TMEM lane (tile row) per thread.  Seven FP32 accumulators of 64 columns
-// occupy 448 of the 512 TMEM columns.  Operands use the no-swizzle K-major
+// through the TMA engine).  Warp 0: copy producer; warp 1: Tensor Memory
+// allocation and the MMA issuer (one thread); warps 2-9: epilogue, two warps
+// per TMEM lane quarter (a warp may read only the lanes of its quarter), 32
+// of the 64 columns each, one TMEM lane (tile row) per thread.  Seven FP32
+// accumulators of 64 columns occupy 448 of the 512 TMEM columns, so the
+// epilogue of a tile and the MMAs of the next do not overlap; a second
+// epilogue warp per quarter halves the epilogue instead.  Operands use the no-swizzle K-major
 // canonical layout (8-row x 16-byte core matrices).
 #include <cuda_runtime.h>
 
@@ -71,7 +73,8 @@ constexpr int kTcNacc = kTcDmax - 1;      // accumulators G_2 .. G_8
 constexpr uint32_t kXBytes = kTcM * kTcK * 2;   // one X slice tile, BF16
 constexpr uint32_t kYBytes = kTcN * kTcK * 2;   // one Y slice half, BF16
 constexpr int kXBufs = 3;
-constexpr int kTcThreads = 192;
+constexpr int kTcEpiWarps = 8;            // two per TMEM lane quarter, 32 columns each
+constexpr int kTcThreads = 64 + 32 * kTcEpiWarps;
 constexpr uint32_t kTmemCols = 512;
 constexpr uint64_t kTcTimeoutNs = 1000000000ull;  // 1 s per wait
 // Limit of the pipeline waits (producer, MMA issuer, epilogue); the drain
@@ -333,7 +336,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_grade_kernel(const TcGemmArg
       tc::mbar_init(b_xempty0 + 8 * b, 1);
     }
     tc::mbar_init(b_accfull, 1);
-    tc::mbar_init(b_accempty, 128);
+    tc::mbar_init(b_accempty, 32 * kTcEpiWarps);
     tc::mbar_init(b_drain, 1);
     *abort_flag = 0;
     tc::mbar_init_fence();
@@ -435,7 +438,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_grade_kernel(const TcGemmArg
     }
   } else {
     // ---- epilogue: thread = TMEM lane = tile row ----
-    const int q = warp & 3;
+    const int q = warp & 3;   // TMEM lane quarter this warp may access
+    const int c_lo = ((warp - 2) / 4) * (kTcN * 4 / kTcEpiWarps);   // its columns: c_lo .. c_lo + 31
     const int rl = q * 32 + lane;
     const uint32_t lane_base = tmem + ((uint32_t)(q * 32) << 16);
     int tcount = 0;
@@ -451,7 +455,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_grade_kernel(const TcGemmArg
       const int e_i = valid ? p.erow[row] : 0;
       int best_e = INT_MIN;
       unsigned long long best_m = 0ull;
-      for (int c0 = 0; c0 < kTcN; c0 += 8) {
+      for (int c0 = c_lo; c0 < c_lo + kTcN * 4 / kTcEpiWarps; c0 += 8) {
         uint32_t v[kTcNacc][8];
 #pragma unroll
         for (int a = 0; a < kTcNacc; ++a) tc::tmem_ld8(lane_base + (uint32_t)(a * kTcN + c0), v[a]);
