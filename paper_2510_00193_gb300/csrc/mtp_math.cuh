@@ -7,6 +7,8 @@
 #define __device__
 #define __host__
 #define __forceinline__ inline
+// host compilation of the generated code (tests): one thread stands for the warp
+inline void __syncwarp(unsigned = 0xffffffffu) {}
 #endif
 
 namespace mtp {
