@@ -39,8 +39,9 @@ import numpy as np
 # levels from which the contraction runs as an interpreted program
 INTERPRET_FROM_LEVEL = 18
 # levels whose neighbour sweeps work on the components with a z-exponent of at
-# most 1 (the others follow from |rhat| = 1 in the contraction)
-SPHERE_MAX_LEVEL = 16
+# most 1 (the others follow from |rhat| = 1 in the contraction, or in the
+# first records of an interpreted contraction program)
+SPHERE_MAX_LEVEL = 20
 
 # ---------------------------------------------------------------------------
 # graphs and basis functions
@@ -1083,6 +1084,13 @@ def emit_contract_program(lv: Level):
         return base[n] + multi_indices(rank).index(K)
 
     prog, starts = [], []
+    # moment components the sweeps leave out (z-exponent >= 2), formed first
+    # from the swept ones: V[c] = V[s0] - V[s1] - V[s2] (the reverse pass then
+    # adds their adjoints into the swept components)
+    for c in sorted(lv.expand, key=lambda t: (lv.comps[t][1][2], t)):
+        s0, s1, s2 = lv.expand[c]
+        starts.append(len(prog))
+        prog += [0, c, 3, s0, one, 1, s1, one, -1, s2, one, -1]
     for n, (key, rank) in enumerate(dag.nodes):
         if key[0] != "C":
             continue
@@ -1168,12 +1176,13 @@ def emit_groups(lv: Level):
         L.append("  template <class R>")
         L.append("  __device__ __forceinline__ static void store_g%d(const R* __restrict__ Mg, R* __restrict__ M, "
                  "int64_t ld) {" % g)
-        L += ["    M[%d * ld] = Mg[%d];" % (c, c) for c in grp]
+        # only swept components travel (the others are formed in the contraction)
+        L += ["    M[%d * ld] = Mg[%d];" % (c, c) for c in grp if c not in lv.expand]
         L.append("  }")
         L.append("  template <class R>")
         L.append("  __device__ __forceinline__ static void load_g%d(const R* __restrict__ D, int64_t ld, "
                  "R* __restrict__ Dg) {" % g)
-        L += ["    Dg[%d] = D[%d * ld];" % (c, c) for c in grp]
+        L += ["    Dg[%d] = D[%d * ld];" % (c, c) for c in grp if c not in lv.expand]
         L.append("  }")
     for grp in lv.groups:
         assert sorted(grp) == list(range(min(grp), max(grp) + 1)), "component groups are contiguous ranges"
