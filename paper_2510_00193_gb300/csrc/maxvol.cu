@@ -86,10 +86,17 @@ __global__ void mv_gauss_jordan_kernel(double* __restrict__ aug, int m, int* __r
     for (int c = threadIdx.x; c < w; c += blockDim.x) aug[(int64_t)col * w + c] = __ddiv_rn(aug[(int64_t)col * w + c], p);
     for (int r = threadIdx.x; r < m; r += blockDim.x) s_f[r] = aug[(int64_t)r * w + col];
     __syncthreads();
-    for (int64_t t = threadIdx.x; t < (int64_t)m * w; t += blockDim.x) {
-      const int r = (int)(t / w), c = (int)(t % w);
-      const double f = s_f[r];
-      if (r != col && f != 0.0) aug[t] = __dsub_rn(aug[t], __dmul_rn(f, aug[(int64_t)col * w + c]));
+    // one thread per column, down the column (coalesced across the warp).
+    // Columns left of col are unit vectors and columns whose pivot-row entry
+    // is zero are unchanged by the update (x - f * 0 = x exactly), so only
+    // the others are visited; every update keeps its separate roundings.
+    for (int c = col + threadIdx.x; c < w; c += blockDim.x) {
+      const double pc = aug[(int64_t)col * w + c];
+      if (pc == 0.0) continue;
+      for (int r = 0; r < m; ++r) {
+        const double f = s_f[r];
+        if (r != col && f != 0.0) aug[(int64_t)r * w + c] = __dsub_rn(aug[(int64_t)r * w + c], __dmul_rn(f, pc));
+      }
     }
     __syncthreads();
   }
@@ -139,8 +146,14 @@ __global__ void __launch_bounds__(kMvThreads) mv_product_kernel(const double* __
   }
 }
 
+// Device-side step state of mtp_maxvol (so that a run of swaps needs no host
+// round trip): st[0] stop decided, st[1] swaps made, st[2] swaps since the
+// last refresh, st[3] non-finite C, st[4] this step swaps; sel = (i, k).
+enum { kMvDone = 0, kMvIt = 1, kMvSince = 2, kMvBad = 3, kMvAct = 4, kMvState = 8 };
+
 // Largest |C| with the first flat index among equal values: per-block
-// candidates, then one block over the candidates.
+// candidates, then one block over the candidates (nothing once a stop is
+// decided).
 __device__ __forceinline__ void mv_better(double& v, long long& i, double v2, long long i2) {
   if (v2 > v || (v2 == v && i2 < i)) {
     v = v2;
@@ -149,7 +162,8 @@ __device__ __forceinline__ void mv_better(double& v, long long& i, double v2, lo
 }
 
 __global__ void mv_argmax_kernel(const double* __restrict__ c, long long total, double* __restrict__ bv,
-                                 long long* __restrict__ bi) {
+                                 long long* __restrict__ bi, const int* __restrict__ st) {
+  if (st[kMvDone]) return;   // grid-uniform
   __shared__ double sv[kMvThreads];
   __shared__ long long si[kMvThreads];
   double v = -1.0;
@@ -174,7 +188,9 @@ __global__ void mv_argmax_kernel(const double* __restrict__ c, long long total, 
 }
 
 __global__ void mv_argmax_final_kernel(const double* __restrict__ bv, const long long* __restrict__ bi, int nb,
-                                       double* __restrict__ out_v, long long* __restrict__ out_i) {
+                                       double* __restrict__ out_v, long long* __restrict__ out_i,
+                                       const int* __restrict__ st) {
+  if (st[kMvDone]) return;
   __shared__ double sv[kMvThreads];
   __shared__ long long si[kMvThreads];
   double v = -1.0;
@@ -193,11 +209,42 @@ __global__ void mv_argmax_final_kernel(const double* __restrict__ bv, const long
   }
 }
 
+// The MaxVol decision on the argmax (v, flat index): stop when v <= 1 +
+// delta or max_iter swaps are made, else swap pool row i into slot k.
+__global__ void mv_decide_kernel(const double* __restrict__ best_v, const long long* __restrict__ best_i, int m,
+                                 double delta, int max_iter, int* __restrict__ st, long long* __restrict__ sel,
+                                 int32_t* __restrict__ rows) {
+  st[kMvAct] = 0;
+  if (st[kMvDone]) return;
+  const double v = *best_v;
+  if (!isfinite(v)) {
+    st[kMvBad] = 1;
+    st[kMvDone] = 1;
+    return;
+  }
+  if (v <= 1.0 + delta || st[kMvIt] >= max_iter) {
+    st[kMvDone] = 1;
+    return;
+  }
+  const long long flat = *best_i;
+  const long long i = flat / m;
+  const int k = (int)(flat % m);
+  sel[0] = i;
+  sel[1] = k;
+  rows[k] = (int32_t)i;
+  st[kMvIt] += 1;
+  st[kMvSince] += 1;
+  st[kMvAct] = 1;
+}
+
 // Snapshot before a swap of row k for pool row i: u = C[:, k] (n), w = (c_i - e_k) / C_ik (m),
-// q = A^-1[:, k] (m).
+// q = A^-1[:, k] (m).  Nothing when the step made no swap.
 __global__ void mv_snapshot_kernel(const double* __restrict__ c, int64_t n, int m, const double* __restrict__ a_inv,
-                                   int64_t i, int k, double* __restrict__ u, double* __restrict__ w,
-                                   double* __restrict__ q) {
+                                   const long long* __restrict__ sel, const int* __restrict__ st,
+                                   double* __restrict__ u, double* __restrict__ w, double* __restrict__ q) {
+  if (!st[kMvAct]) return;
+  const int64_t i = sel[0];
+  const int k = (int)sel[1];
   const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (t < n) u[t] = c[t * m + k];
   if (t < m) {
@@ -207,10 +254,11 @@ __global__ void mv_snapshot_kernel(const double* __restrict__ c, int64_t n, int 
   }
 }
 
-// C -= u w (n x m), A^-1 -= q w (m x m).
+// C -= u w (n x m), A^-1 -= q w (m x m).  Nothing when the step made no swap.
 __global__ void mv_rank1_kernel(double* __restrict__ c, int64_t n, int m, double* __restrict__ a_inv,
                                 const double* __restrict__ u, const double* __restrict__ w,
-                                const double* __restrict__ q) {
+                                const double* __restrict__ q, const int* __restrict__ st) {
+  if (!st[kMvAct]) return;
   const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int64_t nc = n * m;
   if (t < nc) {
@@ -236,15 +284,15 @@ struct MvScratch {
   long long* bi;     // [nb]
   double* best_v;    // [1]
   long long* best_i; // [1]
-  int32_t* rows;     // [m]
+  int32_t* rows;     // [m] the current active rows (device copy, updated by mv_decide_kernel)
   int* singular;     // [1]
+  int* st;           // [kMvState] step state
+  long long* sel;    // [2] (i, k) of the step's swap
   int nb;
 };
 
-// A^-1 of P[rows] into a_inv and C = P A^-1; MTP_ERR_ARG if singular.
-int mv_refresh(const double* pool, int64_t n, int m, const int32_t* h_rows, double* a_inv, MvScratch& sc,
-               cudaStream_t s) {
-  MTP_TRY_CUDA(cudaMemcpyAsync(sc.rows, h_rows, sizeof(int32_t) * m, cudaMemcpyHostToDevice, s));
+// A^-1 of P[rows] into a_inv and C = P A^-1 (rows: sc.rows); MTP_ERR_ARG if singular.
+int mv_refresh(const double* pool, int64_t n, int m, double* a_inv, MvScratch& sc, cudaStream_t s) {
   MTP_TRY_CUDA(cudaMemsetAsync(sc.singular, 0, sizeof(int), s));
   const int64_t na = (int64_t)m * 2 * m;
   mv_gather_kernel<<<(unsigned)((na + kMvThreads - 1) / kMvThreads), kMvThreads, 0, s>>>(pool, sc.rows, m, sc.aug);
@@ -264,17 +312,23 @@ int mv_refresh(const double* pool, int64_t n, int m, const int32_t* h_rows, doub
   return MTP_OK;
 }
 
-int mv_argmax(int64_t n, int m, MvScratch& sc, cudaStream_t s, double* v, int64_t* i, int* k) {
+// One MaxVol step on the device: argmax of |C|, the decision, and (if it
+// swaps) the rank-one updates of C and A^-1.
+int mv_step(int64_t n, int m, double delta, int max_iter, double* a_inv, MvScratch& sc, cudaStream_t s) {
   const long long total = (long long)n * m;
-  mv_argmax_kernel<<<sc.nb, kMvThreads, 0, s>>>(sc.c, total, sc.bv, sc.bi);
-  mv_argmax_final_kernel<<<1, kMvThreads, 0, s>>>(sc.bv, sc.bi, sc.nb, sc.best_v, sc.best_i);
-  MTP_TRY_CUDA(cudaGetLastError());
-  long long flat = 0;
-  MTP_TRY_CUDA(cudaMemcpyAsync(v, sc.best_v, sizeof(double), cudaMemcpyDeviceToHost, s));
-  MTP_TRY_CUDA(cudaMemcpyAsync(&flat, sc.best_i, sizeof(long long), cudaMemcpyDeviceToHost, s));
-  MTP_TRY_CUDA(cudaStreamSynchronize(s));
-  *i = flat / m;
-  *k = (int)(flat % m);
+  mv_argmax_kernel<<<sc.nb, kMvThreads, 0, s>>>(sc.c, total, sc.bv, sc.bi, sc.st);
+  mv_argmax_final_kernel<<<1, kMvThreads, 0, s>>>(sc.bv, sc.bi, sc.nb, sc.best_v, sc.best_i, sc.st);
+  mv_decide_kernel<<<1, 1, 0, s>>>(sc.best_v, sc.best_i, m, delta, max_iter, sc.st, sc.sel, sc.rows);
+  const unsigned gs = (unsigned)((std::max<int64_t>(n, m) + kMvThreads - 1) / kMvThreads);
+  mv_snapshot_kernel<<<gs, kMvThreads, 0, s>>>(sc.c, n, m, a_inv, sc.sel, sc.st, sc.u, sc.w, sc.q);
+  const int64_t tot = (int64_t)n * m + (int64_t)m * m;
+  mv_rank1_kernel<<<(unsigned)((tot + kMvThreads - 1) / kMvThreads), kMvThreads, 0, s>>>(sc.c, n, m, a_inv, sc.u,
+                                                                                         sc.w, sc.q, sc.st);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) {
+    set_error("mtp_maxvol: %s", cudaGetErrorString(e));
+    return MTP_ERR_CUDA;
+  }
   return MTP_OK;
 }
 
@@ -307,7 +361,8 @@ int mtp_maxvol(const double* pool, int64_t n_pool, int32_t m, int32_t* rows, dou
   sc.nb = (int)std::min<int64_t>(4 * 152, ((int64_t)n_pool * m + kMvThreads - 1) / kMvThreads);
   const size_t n = (size_t)n_pool, mm = (size_t)m;
   const size_t bytes = sizeof(double) * (2 * mm * mm + n * mm + n + 2 * mm + (size_t)sc.nb + 1) +
-                       sizeof(long long) * ((size_t)sc.nb + 1) + sizeof(int32_t) * mm + sizeof(int) + 256;
+                       sizeof(long long) * ((size_t)sc.nb + 1 + 2) + sizeof(int32_t) * mm +
+                       sizeof(int) * (1 + kMvState) + 256;
   DevBuf buf;
   int rc = buf.ensure(bytes);
   if (rc != MTP_OK) return rc;
@@ -321,54 +376,57 @@ int mtp_maxvol(const double* pool, int64_t n_pool, int32_t m, int32_t* rows, dou
   sc.best_v = sc.bv + sc.nb;
   sc.bi = reinterpret_cast<long long*>(sc.best_v + 1);
   sc.best_i = sc.bi + sc.nb;
-  sc.rows = reinterpret_cast<int32_t*>(sc.best_i + 1);
+  sc.sel = sc.best_i + 1;
+  sc.rows = reinterpret_cast<int32_t*>(sc.sel + 2);
   sc.singular = reinterpret_cast<int*>(sc.rows + mm);
+  sc.st = sc.singular + 1;
 
-  std::vector<int32_t> cur(rows, rows + m);
-  int it = 0, since = 0;
-  if ((rc = mv_refresh(pool, n_pool, m, cur.data(), a_inv, sc, s)) != MTP_OK) {
+  // The swaps run on the device (mv_step); the host waits once per run of
+  // up to kRefresh - since steps, then refreshes C and A^-1 where the
+  // sequential algorithm would: after kRefresh swaps, and when a stop was
+  // decided on updated rather than freshly computed C.
+  int st[kMvState] = {0};
+  MTP_TRY_CUDA(cudaMemcpyAsync(sc.rows, rows, sizeof(int32_t) * m, cudaMemcpyHostToDevice, s));
+  MTP_TRY_CUDA(cudaMemsetAsync(sc.st, 0, sizeof(int) * kMvState, s));
+  if ((rc = mv_refresh(pool, n_pool, m, a_inv, sc, s)) != MTP_OK) {
     buf.release();
     return rc;
   }
   while (true) {
-    double v = 0.0;
-    int64_t i = 0;
-    int k = 0;
-    if ((rc = mv_argmax(n_pool, m, sc, s, &v, &i, &k)) != MTP_OK) break;
-    if (!std::isfinite(v)) {
+    for (int b = st[kMvSince]; b < kRefresh && rc == MTP_OK; ++b) rc = mv_step(n_pool, m, delta, max_iter, a_inv, sc, s);
+    if (rc != MTP_OK) break;
+    if (cudaMemcpyAsync(st, sc.st, sizeof(int) * kMvState, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess) {
+      set_error("mtp_maxvol: %s", cudaGetErrorString(cudaGetLastError()));
+      rc = MTP_ERR_CUDA;
+      break;
+    }
+    if (st[kMvBad]) {
       set_error("mtp_maxvol: non-finite entry in P A^-1");
       rc = MTP_ERR_NONFINITE;
       break;
     }
-    if (v <= 1.0 + delta || it >= max_iter) {
-      if (since == 0) break;   // decided on freshly computed C
-      if ((rc = mv_refresh(pool, n_pool, m, cur.data(), a_inv, sc, s)) != MTP_OK) break;
-      since = 0;
-      continue;
-    }
-    const unsigned gs = (unsigned)((std::max<int64_t>(n_pool, m) + kMvThreads - 1) / kMvThreads);
-    mv_snapshot_kernel<<<gs, kMvThreads, 0, s>>>(sc.c, n_pool, m, a_inv, i, k, sc.u, sc.w, sc.q);
-    const int64_t tot = (int64_t)n_pool * m + (int64_t)m * m;
-    mv_rank1_kernel<<<(unsigned)((tot + kMvThreads - 1) / kMvThreads), kMvThreads, 0, s>>>(sc.c, n_pool, m, a_inv,
-                                                                                           sc.u, sc.w, sc.q);
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) {
-      set_error("mtp_maxvol: %s", cudaGetErrorString(e));
+    if (st[kMvDone] && st[kMvSince] == 0) break;   // decided on freshly computed C
+    if (!st[kMvDone] && st[kMvSince] < kRefresh) continue;
+    // a stop on updated C, or kRefresh swaps since the last refresh
+    if ((rc = mv_refresh(pool, n_pool, m, a_inv, sc, s)) != MTP_OK) break;
+    st[kMvDone] = 0;
+    st[kMvSince] = 0;
+    if (cudaMemcpyAsync(sc.st, st, sizeof(int) * kMvState, cudaMemcpyHostToDevice, s) != cudaSuccess) {
+      set_error("mtp_maxvol: %s", cudaGetErrorString(cudaGetLastError()));
       rc = MTP_ERR_CUDA;
       break;
     }
-    cur[k] = (int32_t)i;
-    ++it;
-    if (++since >= kRefresh) {
-      if ((rc = mv_refresh(pool, n_pool, m, cur.data(), a_inv, sc, s)) != MTP_OK) break;
-      since = 0;
-    }
+  }
+  std::vector<int32_t> cur((size_t)m);
+  if (rc == MTP_OK) {
+    if (cudaMemcpyAsync(cur.data(), sc.rows, sizeof(int32_t) * m, cudaMemcpyDeviceToHost, s) != cudaSuccess) rc = MTP_ERR_CUDA;
   }
   cudaStreamSynchronize(s);
   buf.release();
   if (rc != MTP_OK) return rc;
   std::memcpy(rows, cur.data(), sizeof(int32_t) * m);
-  if (iterations) *iterations = it;
+  if (iterations) *iterations = st[kMvIt];
   return MTP_OK;
 }
 
