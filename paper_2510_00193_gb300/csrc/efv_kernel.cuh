@@ -378,9 +378,9 @@ constexpr int kMaxWarps = 8;   // blocks of up to 256 threads
 
 template <class R, int NMU, bool DTHETA>
 __host__ __device__ __forceinline__ size_t efv_smem_bytes(int SS, int nq, int m) {
-  // ... then the per-species atom counts and one 8-byte discard slot
+  // ... then the per-species atom counts and one 8-byte discard slot per warp
   return efv_red_offset<R, NMU, DTHETA>(SS, nq, m) + sizeof(double) * 8 * kMaxWarps +
-         ((sizeof(int) * kMaxSpecies + 7) & ~size_t(7)) + sizeof(double);
+         ((sizeof(int) * kMaxSpecies + 7) & ~size_t(7)) + sizeof(double) * kMaxWarps;
 }
 
 // Mixed path with DTHETA: each thread's dE/dc accumulators [zj][mu][k] in
@@ -414,7 +414,7 @@ template <class R> struct WarpBasisSink {
 };
 
 // Consumes each basis value as the contraction forms it: lane 0 of the warp
-// writes it to a shared word that nothing reads.  Used where the basis values
+// writes it to the warp's own shared word, which nothing reads.  Used where the basis values
 // are not wanted: with a use of this kind the level-16 energy/force kernel
 // compiles without stack (the contraction alone fits in its registers);
 // without one, ptxas keeps values of the contraction live into the adjoint
@@ -444,7 +444,7 @@ struct EfvShared {
   R* acc;     // mixed DTHETA: per-thread dE/dc accumulators [S NMU nq][blockDim], or null
   double* red;
   int* cnt;   // [S]
-  R* discard; // one word that DiscardBasisSink writes and nothing reads
+  R* discard; // [kMaxWarps] words that DiscardBasisSink writes and nothing reads
   int S, SS, nq, cstride, m;
   R rcut, mid, scale, rmin;
 
@@ -766,7 +766,7 @@ __device__ __forceinline__ void efv_atom(const EfvArgs& a, const EfvShared<R, LV
         M, sm.xi, D, WarpBasisSink<R>{sm.dxi, (int)(threadIdx.x & 31), active});
   } else if constexpr (!DTHETA && LV::NGROUPS == 1) {
     ei = contract_atom<LV, DAG, R, true, const R*, DiscardBasisSink<R>>(
-        M, sm.xi, D, DiscardBasisSink<R>{sm.discard, (threadIdx.x & 31) == 0});
+        M, sm.xi, D, DiscardBasisSink<R>{sm.discard + (threadIdx.x >> 5), (threadIdx.x & 31) == 0});
   } else {
     R Bv[DTHETA ? LV::NBASIS : 1];
     ei = LV::template contract<R, DTHETA>(M, sm.xi, D, Bv);

@@ -91,7 +91,7 @@ __global__ void __launch_bounds__(kEfvThreads) efv_team_kernel(const EfvArgs a) 
       ei = LV::template contract<R, true>(M, sm.xi, D, Bv);
     else
       ei = LV::template contract<R, true, const R*, DiscardBasisSink<R>>(
-          M, sm.xi, D, DiscardBasisSink<R>{sm.discard, lane == 0});
+          M, sm.xi, D, DiscardBasisSink<R>{sm.discard + warp, lane == 0});
     if (lane == 0) {
       e_i = a.species_energy[zi] + (double)ei;
       a.e_atom[i] = e_i;
